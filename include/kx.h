@@ -1,0 +1,191 @@
+/*
+ * kx.h -- C ABI of the GB300 exponential-Krylov Maxwell solver.
+ *
+ * Method: Botchev, Hanse & Uppu, "Exponential Krylov time integration for
+ * modeling multi-frequency optical response with monochromatic sources"
+ * (arXiv:1707.00023).  The library solves the semi-discrete Maxwell system
+ *
+ *     y'(t) = -A y(t) + sin(Omega t) g,   y(0) = 0          (eq. (ode))
+ *
+ * on a Yee grid, by exponential Krylov methods: the plain time-restarted
+ * method on the system augmented with the source phase, and the asymptotic
+ * splitting y = Im(e^{i Omega t} z) - exp(-tA) Im z with z = (A + i Omega I)^{-1} g
+ * (eq. (split1)), whose stationary parts for many frequencies share one
+ * Krylov basis (Corollary 1).
+ *
+ * Conventions shared by every entry point:
+ *  - Field vectors are CALLER-OWNED DEVICE arrays of n = ncomp * ncell
+ *    scalars in the context's precision (double for KX_FP64, float for
+ *    KX_FP32).  Layout: component-major [Hx, Hy, Ez] (2D) or
+ *    [Hx, Hy, Hz, Ex, Ey, Ez] (3D); within a component x is fastest, then y,
+ *    then z.  Nodes on a conducting wall (integer coordinate along a PEC
+ *    axis at index 0) are not unknowns: input values there are ignored and
+ *    outputs there are 0.
+ *  - Small arrays (H, u, omegas, results) may be host or device memory
+ *    where stated; the library tells them apart itself.
+ *  - Every call is ordered on the CUDA stream given at creation.  Calls
+ *    that return host values synchronise that stream.  The context owns all
+ *    workspace (allocated at creation); the compute calls allocate nothing.
+ *  - Every call returns a kx_status and never aborts or prints; the reason
+ *    of the last failure is kept in kx_last_error(ctx).  A context is not
+ *    thread-safe: use one per stream.
+ */
+#ifndef KX_H
+#define KX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KX_OK = 0,
+  KX_EINVAL = 1,      /* bad argument or descriptor                        */
+  KX_ENOMEM = 2,      /* device or host allocation failed (creation only)  */
+  KX_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed       */
+  KX_ENONFINITE = 4,  /* NaN/Inf met in an input or a reduction            */
+  KX_ENOCONV = 5,     /* iteration cap reached; partial result returned    */
+  KX_ETIMEOUT = 6     /* a bounded device-side wait ran out                */
+} kx_status;
+
+enum { KX_PERIODIC = 0, KX_PEC = 1 };
+enum { KX_FP64 = 0, KX_FP32 = 1 };
+enum { KX_PLAIN = 0, KX_SPLIT = 1 };
+
+/* Problem descriptor.  Grid of n[0] x n[1] (x n[2]) unit cells; the
+ * absorbing layer (conductivity ramping linearly from 0 to sigma_max over
+ * layer_cells cells at both ends of layer_axis) lies inside the grid.  The
+ * conductivity of a node is sigma_max * d / layer_cells with d the depth of
+ * the node's own staggered coordinate into the layer (Sect. 2.1 damping
+ * terms; a plain lossy layer, no auxiliary PML variable). */
+typedef struct {
+  int dim;            /* 2 (fields Hx, Hy, Ez) or 3 (Hx, Hy, Hz, Ex, Ey, Ez) */
+  int n[3];           /* cells along x, y, z (n[2] ignored when dim == 2); each >= 3 */
+  int bc[3];          /* KX_PERIODIC or KX_PEC per axis                      */
+  int layer_axis;     /* 0 .. dim-1                                          */
+  int layer_cells;    /* >= 1, 2 * layer_cells <= n[layer_axis]              */
+  double sigma_max;   /* >= 0                                                */
+  int precision;      /* KX_FP64 or KX_FP32 (vectors); projected work is FP64 */
+  int krylov_dim;     /* m, 2 <= m <= 64: Arnoldi steps per restart          */
+  int max_freqs;      /* largest nfreq of any later call, 1 .. 64            */
+  int batch;          /* bases held for concurrent transients, >= 1          */
+} kx_desc;
+
+typedef struct kx_ctx kx_ctx;
+
+/* Per-context counters since creation (or the last kx_reset_stats). */
+typedef struct {
+  int64_t matvecs;         /* applications of A (one per Arnoldi step)   */
+  int64_t arnoldi_steps;
+  int64_t substeps;        /* accepted time sub-steps                     */
+  int64_t expm_evals;      /* projected exponentials                      */
+  int64_t fom_cycles;      /* restarts of the shifted FOM                 */
+  int64_t kernel_launches; /* kernels this library launched               */
+} kx_stats;
+
+/* Create a context.  eps_cell: HOST array of n[0]*n[1](*n[2]) per-cell
+ * relative permittivities (> 0, finite), x fastest; mu_r = 1 (Sect. 2.1).
+ * The permittivity of an E node is the mean over the cells whose closure
+ * holds the node.  stream: a cudaStream_t (NULL = legacy default stream).
+ * All workspace (batch Krylov bases of krylov_dim + 1 vectors, projected
+ * matrices, reduction buffers) is allocated here.
+ * Errors: KX_EINVAL (descriptor), KX_ENONFINITE (eps), KX_ENOMEM. */
+kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell,
+                             void* cuda_stream, kx_ctx** out);
+
+/* Release a context and its workspace.  NULL is accepted. */
+kx_status krylov_expm_destroy(kx_ctx* ctx);
+
+/* Number of unknowns n (including wall nodes) of the context's grid. */
+int64_t kx_num_unknowns(const kx_ctx* ctx);
+
+/* w = A v (transpose = 0) or w = A^T v (transpose = 1), A the matrix of
+ * eq. (ode): H rows sigma H + curl E, E rows (sigma E - curl H) / eps.
+ * d_v, d_w: device vectors of n scalars, must not overlap.  Asynchronous. */
+kx_status apply_A(kx_ctx* ctx, const void* d_v, void* d_w, int transpose);
+
+/* m steps of the Arnoldi process for K_m(A, v0) (Sect. 3.2, eqs. (Arn),
+ * (Arn1)): A V_m = V_{m+1} H, v_1 = v0/||v0||.  Classical Gram-Schmidt,
+ * dots fused with the operator application.
+ *   d_v0  : device, n scalars (not modified).
+ *   m     : 1 .. krylov_dim.
+ *   d_V   : device n x (m+1) column-major (leading dim n) receiving the
+ *           orthonormal basis, or NULL.
+ *   H     : (m+1) x m column-major FP64, host or device, zero-filled then
+ *           written.
+ *   beta  : host, receives ||v0||.     m_done: host, steps done (< m only
+ *           after a lucky breakdown, h_{j+1,j} ~ 0; then columns past
+ *           m_done of d_V are zero).
+ * Synchronises the stream.  Errors: KX_EINVAL, KX_ENONFINITE (v0 = 0 or
+ * non-finite). */
+kx_status arnoldi(kx_ctx* ctx, const void* d_v0, int m, void* d_V, double* H,
+                  double* beta, int* m_done);
+
+/* Projected solutions (eq. (corr2); Corollary 1).  H: (m+1) x m upper
+ * Hessenberg (only the leading m x m block is used), leading dimension
+ * ldh >= m, FP64, host or device.
+ *   nfreq == 0: u = exp(-tau H_m) beta e_1                   (m values)
+ *   nfreq >= 1: u_j = u(tau) of u' = -H_m u + sin(omega_j t) beta e_1,
+ *               u(0) = 0, for each omega_j (host array)      (m x nfreq)
+ * Evaluated by FP64 scaling-and-squaring Pade (Higham 2005) of the
+ * (m+2) x (m+2) matrix that carries the source phase.  u_out: host or
+ * device, column-major m x max(1, nfreq).  m <= krylov_dim, nfreq <=
+ * max_freqs.  Synchronises the stream. */
+kx_status expm_phi_project(kx_ctx* ctx, const double* H, int ldh, int m,
+                           double beta, double tau, const double* omegas,
+                           int nfreq, double* u_out);
+
+/* Stationary parts z_j = (A + i omega_j I)^{-1} g for all j (eq. (split1)),
+ * by restarted shifted FOM on ONE real Krylov basis per restart (the
+ * residuals of all shifts stay collinear with v_{m+1}, eq. (Arn1)).
+ *   d_g: device n scalars.  omegas: host nfreq (1 .. max_freqs).
+ *   rtol: stop when every |rho_j| <= rtol ||g||.  max_matvecs: cap (> 0).
+ *   d_z_re, d_z_im: device n x nfreq column-major (leading dim n).
+ *   rel_resid: host nfreq, TRUE relative residuals ||g - (A+i w)z||/||g||
+ *              (or NULL).  matvecs: host, applications of A used (or NULL).
+ * Returns KX_ENOCONV (with the partial z) if the cap is hit first.
+ * Synchronises the stream. */
+kx_status stationary_solve(kx_ctx* ctx, const void* d_g, const double* omegas,
+                           int nfreq, double rtol, int max_matvecs,
+                           void* d_z_re, void* d_z_im, double* rel_resid,
+                           int* matvecs);
+
+/* y = exp(-T A) y0 (the homogeneous problem eq. (y_homo)) by exponential
+ * Krylov restarted in time; each sub-step's length is chosen so that the
+ * integrated Lemma 1 residual stays below rtol * ||y0|| * (sub-step / T).
+ * d_y0, d_y: device n scalars (may be equal).  err_est: host (or NULL).
+ * Synchronises the stream. */
+kx_status expm_action(kx_ctx* ctx, const void* d_y0, double T, double rtol,
+                      void* d_y, double* err_est);
+
+/* Frequency responses y_j(T) of eq. (ode) (v = 0, alpha = sin(omega_j t)).
+ *   method KX_PLAIN: exponential Krylov restarted in time on the system
+ *     augmented with the source phase, one frequency at a time.
+ *   method KX_SPLIT: eq. (split1) with all stationary parts from one
+ *     shifted solve (stationary_solve) and the transients exp(-TA) Im z_j by
+ *     expm_action (Fig. alg:spl1 steps 1-3 for each frequency).
+ *   plane: host int[2] = {axis, index}: output plane perpendicular to axis.
+ *   d_E_plane: device, nfreq x nE x (plane nodes) scalars (nE = 1 in 2D:
+ *     Ez; 3 in 3D: Ex, Ey at the plane, Ez half a cell above), or NULL.
+ *   intensity: host nfreq, summed |E|^2 over the plane (or NULL).
+ *   err_est: host nfreq, a-posteriori error estimates (or NULL).
+ *   d_Y: device n x nfreq full fields y_j(T), or NULL.
+ * Synchronises the stream.  KX_ENOCONV if a stationary solve hit its cap. */
+kx_status response_at_freqs(kx_ctx* ctx, const void* d_g, const double* omegas,
+                            int nfreq, double T, double rtol, int method,
+                            const int* plane, void* d_E_plane, double* intensity,
+                            double* err_est, void* d_Y);
+
+/* Counters; kx_reset_stats zeroes them. */
+kx_status kx_get_stats(const kx_ctx* ctx, kx_stats* out);
+kx_status kx_reset_stats(kx_ctx* ctx);
+
+/* Text of the last failure on this context ("" if none).  NULL ctx gives
+ * the last creation failure of the calling thread. */
+const char* kx_last_error(const kx_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KX_H */

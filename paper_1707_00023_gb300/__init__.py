@@ -1,0 +1,12 @@
+"""GB300 exponential-Krylov solver for multi-frequency optical response.
+
+Python face of the C ABI in include/kx.h (Botchev, Hanse & Uppu,
+arXiv:1707.00023).  The compute path is the CUDA library libkx.so built
+in-tree by ``paper_1707_00023_gb300.build``; this package only marshals
+arguments.
+"""
+from ._binding import (KX_FP32, KX_FP64, KX_PEC, KX_PERIODIC, KX_PLAIN, KX_SPLIT, Context,
+                       KxError, EXPORTS, load_library)
+
+__all__ = ["Context", "KxError", "load_library", "EXPORTS", "KX_FP32", "KX_FP64", "KX_PEC",
+           "KX_PERIODIC", "KX_PLAIN", "KX_SPLIT"]

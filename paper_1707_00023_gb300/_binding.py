@@ -1,0 +1,244 @@
+"""ctypes binding of the kx C ABI (include/kx.h).
+
+Argument marshalling only: every numerical step runs in libkx.so's CUDA
+kernels.  PyTorch supplies device memory and the CUDA stream.  There is no
+CPU fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libkx.so")
+
+KX_OK, KX_EINVAL, KX_ENOMEM, KX_ECUDA, KX_ENONFINITE, KX_ENOCONV, KX_ETIMEOUT = range(7)
+KX_PERIODIC, KX_PEC = 0, 1
+KX_FP64, KX_FP32 = 0, 1
+KX_PLAIN, KX_SPLIT = 0, 1
+STATUS_NAMES = {0: "KX_OK", 1: "KX_EINVAL", 2: "KX_ENOMEM", 3: "KX_ECUDA",
+                4: "KX_ENONFINITE", 5: "KX_ENOCONV", 6: "KX_ETIMEOUT"}
+
+EXPORTS = ["krylov_expm_create", "krylov_expm_destroy", "kx_num_unknowns", "apply_A",
+           "arnoldi", "expm_phi_project", "stationary_solve", "expm_action",
+           "response_at_freqs", "kx_get_stats", "kx_reset_stats", "kx_last_error"]
+
+
+class KxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("bc", ctypes.c_int * 3),
+                ("layer_axis", ctypes.c_int), ("layer_cells", ctypes.c_int),
+                ("sigma_max", ctypes.c_double), ("precision", ctypes.c_int),
+                ("krylov_dim", ctypes.c_int), ("max_freqs", ctypes.c_int), ("batch", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("matvecs", ctypes.c_int64), ("arnoldi_steps", ctypes.c_int64),
+                ("substeps", ctypes.c_int64), ("expm_evals", ctypes.c_int64),
+                ("fom_cycles", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None):
+    """Load libkx.so; raise if it is not built (no fallback exists)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIBPATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(p)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    lib.krylov_expm_create.argtypes = [ctypes.POINTER(Desc), dp, vp, ctypes.POINTER(vp)]
+    lib.krylov_expm_destroy.argtypes = [vp]
+    lib.kx_num_unknowns.argtypes = [vp]
+    lib.kx_num_unknowns.restype = ctypes.c_int64
+    lib.apply_A.argtypes = [vp, vp, vp, ctypes.c_int]
+    lib.arnoldi.argtypes = [vp, vp, ctypes.c_int, vp, vp, dp, ip]
+    lib.expm_phi_project.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_double, dp, ctypes.c_int, vp]
+    lib.stationary_solve.argtypes = [vp, vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                     vp, vp, dp, ip]
+    lib.expm_action.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, vp, dp]
+    lib.response_at_freqs.argtypes = [vp, vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, ip, vp, dp, dp, vp]
+    lib.kx_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    lib.kx_reset_stats.argtypes = [vp]
+    lib.kx_last_error.argtypes = [vp]
+    lib.kx_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "kx_num_unknowns" and name != "kx_last_error":
+            getattr(lib, name).restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Context:
+    """One solver context: grid, permittivity, precision and workspace.
+
+    ``grid`` is any object with attributes dim, n, bc, layer_axis,
+    layer_cells, sigma_max (e.g. ``scenario.Grid``).  ``eps_cell`` is the
+    per-cell permittivity (numpy, x fastest).  ``stream``: a torch CUDA
+    stream (default: the current stream).
+    """
+
+    def __init__(self, grid, eps_cell, precision: str = "fp32", krylov_dim: int = 64,
+                 max_freqs: int = 1, batch: int = 1, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        self.grid = grid
+        d = Desc()
+        d.dim = grid.dim
+        n = list(grid.n) + [1] * (3 - len(grid.n))
+        bc = list(grid.bc) + [0] * (3 - len(grid.bc))
+        d.n = (ctypes.c_int * 3)(*n)
+        d.bc = (ctypes.c_int * 3)(*bc)
+        d.layer_axis = grid.layer_axis
+        d.layer_cells = grid.layer_cells
+        d.sigma_max = grid.sigma_max
+        d.precision = KX_FP64 if precision == "fp64" else KX_FP32
+        d.krylov_dim = krylov_dim
+        d.max_freqs = max_freqs
+        d.batch = batch
+        self.desc = d
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        eps = np.ascontiguousarray(np.asarray(eps_cell, np.float64).reshape(-1))
+        h = ctypes.c_void_p()
+        st = self.lib.krylov_expm_create(ctypes.byref(d), _dptr(eps),
+                                         ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != KX_OK:
+            raise KxError(st, self.lib.kx_last_error(None).decode())
+        self.h = h
+        self.n = int(self.lib.kx_num_unknowns(h))
+
+    # -- helpers -----------------------------------------------------------
+    def _check(self, st):
+        if st != KX_OK:
+            raise KxError(st, self.lib.kx_last_error(self.h).decode())
+
+    def _vec(self, t, name, ncols=1):
+        torch = self._torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != self.dtype:
+            raise TypeError(f"{name} must be {self.dtype}")
+        if not t.is_contiguous() or t.numel() != self.n * ncols:
+            raise ValueError(f"{name} must be contiguous with {self.n * ncols} elements")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def empty(self, *cols):
+        return self._torch.empty((*cols, self.n), dtype=self.dtype, device="cuda")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.krylov_expm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self):
+        s = Stats()
+        self._check(self.lib.kx_get_stats(self.h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def reset_stats(self):
+        self._check(self.lib.kx_reset_stats(self.h))
+
+    # -- ABI calls -----------------------------------------------------------
+    def apply_A(self, v, w=None, transpose=False):
+        if w is None:
+            w = self._torch.empty_like(v)
+        self._check(self.lib.apply_A(self.h, self._vec(v, "v"), self._vec(w, "w"), int(bool(transpose))))
+        return w
+
+    def arnoldi(self, v0, m, want_V=True):
+        V = self.empty(m + 1) if want_V else None
+        H = np.zeros((m, m + 1))       # column-major (m+1) x m as rows of H^T
+        beta = ctypes.c_double()
+        md = ctypes.c_int()
+        self._check(self.lib.arnoldi(self.h, self._vec(v0, "v0"), m,
+                                     ctypes.c_void_p(V.data_ptr()) if V is not None else None,
+                                     H.ctypes.data_as(ctypes.c_void_p), ctypes.byref(beta), ctypes.byref(md)))
+        return V, H.T.copy(), beta.value, md.value
+
+    def expm_phi_project(self, H, beta, tau, omegas: Optional[Sequence[float]] = None):
+        H = np.asarray(H, np.float64)
+        m = H.shape[1]
+        Hc = np.asfortranarray(H[:m, :m])
+        nf = 0 if omegas is None else len(omegas)
+        om = np.ascontiguousarray(np.asarray(omegas if nf else [0.0], np.float64))
+        u = np.zeros((max(1, nf), m))
+        self._check(self.lib.expm_phi_project(self.h, Hc.ctypes.data_as(ctypes.c_void_p), m, m,
+                                              float(beta), float(tau), _dptr(om), nf,
+                                              u.ctypes.data_as(ctypes.c_void_p)))
+        return u[0] if nf == 0 else u
+
+    def stationary_solve(self, g, omegas, rtol=1e-10, max_matvecs=100000, allow_noconv=False):
+        om = np.ascontiguousarray(np.asarray(omegas, np.float64))
+        nf = len(om)
+        zr = self._torch.zeros((nf, self.n), dtype=self.dtype, device="cuda")
+        zi = self._torch.zeros((nf, self.n), dtype=self.dtype, device="cuda")
+        rel = np.zeros(nf)
+        mv = ctypes.c_int()
+        st = self.lib.stationary_solve(self.h, self._vec(g, "g"), _dptr(om), nf, float(rtol), int(max_matvecs),
+                                       ctypes.c_void_p(zr.data_ptr()), ctypes.c_void_p(zi.data_ptr()),
+                                       _dptr(rel), ctypes.byref(mv))
+        if not (allow_noconv and st == KX_ENOCONV):
+            self._check(st)
+        return zr, zi, rel, mv.value
+
+    def expm_action(self, y0, T, rtol=1e-8, out=None):
+        if out is None:
+            out = self._torch.empty_like(y0)
+        err = ctypes.c_double()
+        self._check(self.lib.expm_action(self.h, self._vec(y0, "y0"), float(T), float(rtol),
+                                         self._vec(out, "y"), ctypes.byref(err)))
+        return out, err.value
+
+    def plane_size(self, plane):
+        axis = plane[0]
+        p = 1
+        for a in range(self.grid.dim):
+            if a != axis:
+                p *= self.grid.n[a]
+        return (3 if self.grid.dim == 3 else 1), p
+
+    def response_at_freqs(self, g, omegas, T, rtol=1e-8, method="split", plane=(0, 0),
+                          want_plane=True, want_full=False, allow_noconv=False):
+        om = np.ascontiguousarray(np.asarray(omegas, np.float64))
+        nf = len(om)
+        nE, npl = self.plane_size(plane)
+        Ep = self._torch.empty((nf, nE, npl), dtype=self.dtype, device="cuda") if want_plane else None
+        Y = self.empty(nf) if want_full else None
+        inten = np.zeros(nf)
+        err = np.zeros(nf)
+        pl = (ctypes.c_int * 2)(int(plane[0]), int(plane[1]))
+        st = self.lib.response_at_freqs(
+            self.h, self._vec(g, "g"), _dptr(om), nf, float(T), float(rtol),
+            KX_SPLIT if method == "split" else KX_PLAIN, pl,
+            ctypes.c_void_p(Ep.data_ptr()) if Ep is not None else None, _dptr(inten), _dptr(err),
+            ctypes.c_void_p(Y.data_ptr()) if Y is not None else None)
+        if not (allow_noconv and st == KX_ENOCONV):
+            self._check(st)
+        return {"E_plane": Ep, "intensity": inten, "err_est": err, "Y": Y, "status": st}

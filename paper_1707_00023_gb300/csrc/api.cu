@@ -1,0 +1,548 @@
+// C ABI of the library (declared in include/kx.h): context set-up and the
+// host-side drivers of the Krylov methods.  Every numerical step runs in the
+// library's kernels; the host only sequences launches on the context's
+// stream and reads back small status records.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "kx_internal.cuh"
+
+using namespace kx;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+kx_status fail(kx_ctx* c, kx_status code, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+kx_status cuda_fail(kx_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, KX_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+#define KX_TRY(expr)              \
+  do {                            \
+    kx_status s__ = (expr);       \
+    if (s__ != KX_OK) return s__; \
+  } while (0)
+
+#define KX_CUDA(c, expr, what)                      \
+  do {                                              \
+    cudaError_t e__ = (expr);                       \
+    if (e__ != cudaSuccess) return cuda_fail((c), e__, (what)); \
+  } while (0)
+
+void* vec_ptr(kx_ctx* c, void* base, int64_t col) {
+  return (char*)base + col * c->n * c->esize;
+}
+
+void* slot_col(kx_ctx* c, int slot, int col) {
+  return (char*)c->d_V + ((int64_t)slot * (c->m + 1) + col) * c->ld * c->esize;
+}
+
+kx_status sync(kx_ctx* c) {
+  KX_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronise");
+  return KX_OK;
+}
+
+kx_status upload_state(kx_ctx* c, int slot, const SlotState& s) {
+  c->h_state[slot] = s;
+  KX_CUDA(c, cudaMemcpyAsync(c->d_state + slot, c->h_state + slot, sizeof(SlotState),
+                             cudaMemcpyHostToDevice, c->stream), "state upload");
+  return sync(c);
+}
+
+kx_status read_state(kx_ctx* c, int slot, SlotState* out) {
+  KX_CUDA(c, cudaMemcpyAsync(c->h_state + slot, c->d_state + slot, sizeof(SlotState),
+                             cudaMemcpyDeviceToHost, c->stream), "state read");
+  KX_TRY(sync(c));
+  *out = c->h_state[slot];
+  return KX_OK;
+}
+
+SlotState fresh_state() {
+  SlotState s;
+  std::memset(&s, 0, sizeof(s));
+  return s;
+}
+
+// m Arnoldi steps on slot `slot` from its (already normalised) column 0.
+kx_status arnoldi_steps(kx_ctx* c, int slot, int m, const void* g_aug) {
+  for (int j = 0; j < m; ++j) {
+    KX_TRY(launch_pass_a(c, slot, j, g_aug));
+    KX_TRY(launch_pass_b(c, slot, j));
+  }
+  c->stats.arnoldi_steps += m;
+  c->stats.matvecs += m;
+  return KX_OK;
+}
+
+// Exponential Krylov restarted in time (Sect. 3.3): the state in column 0 of
+// `slot` is advanced to st.T by sub-steps x <- V_m exp(-t H_m) beta e_1.
+kx_status time_loop(kx_ctx* c, int slot, const void* g_aug, double* err_est) {
+  KX_TRY(launch_norm_init(c, slot));
+  const int max_sub = 20000;
+  SlotState st;
+  for (int it = 0; it < max_sub; ++it) {
+    KX_TRY(arnoldi_steps(c, slot, c->m, g_aug));
+    KX_TRY(launch_substep_control(c, slot));
+    KX_TRY(launch_combine(c, slot));
+    KX_TRY(read_state(c, slot, &st));
+    if (st.status) {
+      return fail(c, (kx_status)st.status,
+                  st.status == KX_ENOCONV ? "time sub-step control: no step length met the tolerance"
+                                          : "non-finite value in the Krylov process");
+    }
+    if (st.finished) break;
+  }
+  if (!st.finished) return fail(c, KX_ENOCONV, "time stepping: sub-step cap reached");
+  c->stats.substeps += st.substeps;
+  c->stats.expm_evals += st.expm_evals;
+  if (err_est) *err_est = st.err_acc;
+  return KX_OK;
+}
+
+kx_status check_vec(kx_ctx* c, const void* p, const char* name) {
+  if (!p) return fail(c, KX_EINVAL, std::string(name) + " is NULL");
+  return KX_OK;
+}
+
+kx_status check_omegas(kx_ctx* c, const double* om, int nfreq) {
+  if (nfreq < 1 || nfreq > c->d.max_freqs)
+    return fail(c, KX_EINVAL, "nfreq out of range 1..max_freqs");
+  if (!om) return fail(c, KX_EINVAL, "omegas is NULL");
+  for (int f = 0; f < nfreq; ++f)
+    if (!std::isfinite(om[f])) return fail(c, KX_ENONFINITE, "non-finite frequency");
+  return KX_OK;
+}
+
+// Stationary parts into the buffers zre, zim (n x nfreq, leading dim n).
+kx_status stationary_core(kx_ctx* c, const void* d_g, const double* omegas, int nfreq, double rtol,
+                          int max_matvecs, void* zre, void* zim, double* rel_resid, int* matvecs_out) {
+  const int slot = 0;
+  KX_CUDA(c, cudaMemcpyAsync(slot_col(c, slot, 0), d_g, c->n * c->esize, cudaMemcpyDeviceToDevice,
+                             c->stream), "copy g");
+  KX_TRY(upload_state(c, slot, fresh_state()));
+  KX_TRY(launch_norm_init(c, slot));
+  SlotState st;
+  KX_TRY(read_state(c, slot, &st));
+  const double beta = st.beta;
+  if (!std::isfinite(beta)) return fail(c, KX_ENONFINITE, "non-finite source vector");
+  KX_CUDA(c, cudaMemsetAsync(zre, 0, (size_t)nfreq * c->n * c->esize, c->stream), "zero z");
+  KX_CUDA(c, cudaMemsetAsync(zim, 0, (size_t)nfreq * c->n * c->esize, c->stream), "zero z");
+  if (beta == 0.0) {
+    if (rel_resid) for (int f = 0; f < nfreq; ++f) rel_resid[f] = 0.0;
+    if (matvecs_out) *matvecs_out = 0;
+    return sync(c);
+  }
+  std::vector<double> rho(2 * nfreq);
+  for (int f = 0; f < nfreq; ++f) { rho[2 * f] = beta; rho[2 * f + 1] = 0.0; }
+  KX_CUDA(c, cudaMemcpyAsync(c->d_rho, rho.data(), sizeof(double) * 2 * nfreq, cudaMemcpyHostToDevice,
+                             c->stream), "rho upload");
+  KX_CUDA(c, cudaMemcpyAsync(c->d_omegas, omegas, sizeof(double) * nfreq, cudaMemcpyHostToDevice,
+                             c->stream), "omega upload");
+  KX_TRY(sync(c));
+  int matvecs = 0;
+  bool converged = false;
+  double best = INFINITY;
+  int since_best = 0;
+  for (int cyc = 0; matvecs < max_matvecs; ++cyc) {
+    KX_TRY(arnoldi_steps(c, slot, c->m, nullptr));
+    KX_TRY(read_state(c, slot, &st));
+    if (st.status) return fail(c, (kx_status)st.status, "non-finite value in the Arnoldi process");
+    const int md = st.m_done;
+    KX_TRY(launch_shifted_solve(c, slot, nfreq, md));
+    KX_TRY(launch_zupdate(c, slot, nfreq, zre, zim, md));
+    matvecs += md;
+    c->stats.fom_cycles++;
+    KX_CUDA(c, cudaMemcpyAsync(c->h_small, c->d_rho, sizeof(double) * 2 * nfreq,
+                               cudaMemcpyDeviceToHost, c->stream), "rho read");
+    KX_TRY(sync(c));
+    double worst = 0.0;
+    for (int f = 0; f < nfreq; ++f) worst = std::max(worst, std::hypot(c->h_small[2 * f], c->h_small[2 * f + 1]));
+    if (!std::isfinite(worst)) return fail(c, KX_ENONFINITE, "non-finite shifted-FOM residual");
+    if (worst <= rtol * beta || st.done) { converged = true; break; }
+    // stagnation (rounding floor of the working precision): stop early
+    if (worst < 0.999 * best) { best = worst; since_best = 0; }
+    else if (++since_best >= 20) break;
+    // restart from v_{m+1}: copy column md to column 0 and renormalise
+    KX_CUDA(c, cudaMemcpyAsync(slot_col(c, slot, 0), slot_col(c, slot, md), c->n * c->esize,
+                               cudaMemcpyDeviceToDevice, c->stream), "restart copy");
+    KX_TRY(launch_norm_init(c, slot));
+  }
+  if (matvecs_out) *matvecs_out = matvecs;
+  if (rel_resid) KX_TRY(launch_true_residual(c, d_g, nfreq, omegas, zre, zim, rel_resid));
+  KX_TRY(sync(c));
+  if (!converged) return fail(c, KX_ENOCONV, "shifted FOM: matvec cap reached before rtol");
+  return KX_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* cuda_stream,
+                             kx_ctx** out) {
+  if (!desc || !eps_cell || !out) return fail(nullptr, KX_EINVAL, "NULL argument");
+  *out = nullptr;
+  const kx_desc& d = *desc;
+  if (d.dim != 2 && d.dim != 3) return fail(nullptr, KX_EINVAL, "dim must be 2 or 3");
+  for (int a = 0; a < d.dim; ++a) {
+    if (d.n[a] < 3) return fail(nullptr, KX_EINVAL, "each n[a] must be >= 3");
+    if (d.bc[a] != KX_PERIODIC && d.bc[a] != KX_PEC) return fail(nullptr, KX_EINVAL, "bad bc");
+  }
+  if (d.layer_axis < 0 || d.layer_axis >= d.dim) return fail(nullptr, KX_EINVAL, "bad layer_axis");
+  if (d.layer_cells < 1 || 2 * d.layer_cells > d.n[d.layer_axis])
+    return fail(nullptr, KX_EINVAL, "bad layer_cells");
+  if (!(d.sigma_max >= 0.0) || !std::isfinite(d.sigma_max)) return fail(nullptr, KX_EINVAL, "bad sigma_max");
+  if (d.precision != KX_FP64 && d.precision != KX_FP32) return fail(nullptr, KX_EINVAL, "bad precision");
+  if (d.krylov_dim < 2 || d.krylov_dim > MMAX) return fail(nullptr, KX_EINVAL, "krylov_dim must be 2..64");
+  if (d.max_freqs < 1 || d.max_freqs > MAXF) return fail(nullptr, KX_EINVAL, "max_freqs must be 1..64");
+  if (d.batch < 1 || d.batch > 64) return fail(nullptr, KX_EINVAL, "batch must be 1..64");
+  const int nz = d.dim == 3 ? d.n[2] : 1;
+  const int64_t ncell = (int64_t)d.n[0] * d.n[1] * nz;
+  for (int64_t i = 0; i < ncell; ++i)
+    if (!(eps_cell[i] > 0.0) || !std::isfinite(eps_cell[i]))
+      return fail(nullptr, KX_ENONFINITE, "eps_cell must be finite and > 0");
+
+  kx_ctx* c = new (std::nothrow) kx_ctx();
+  if (!c) return fail(nullptr, KX_ENOMEM, "host allocation failed");
+  c->d = d;
+  if (d.dim == 2) c->d.n[2] = 1;
+  c->stream = (cudaStream_t)cuda_stream;
+  Geo& g = c->geo;
+  g.dim = d.dim;
+  g.nx = d.n[0];
+  g.ny = d.n[1];
+  g.nz = nz;
+  g.ncell = ncell;
+  g.ncomp = d.dim == 2 ? 3 : 6;
+  g.nh = d.dim == 2 ? 2 : 3;
+  g.la = d.layer_axis;
+  // staggered offsets: 1 = half-integer along the axis
+  static const int off2[3][3] = {{0, 1, 0}, {1, 0, 0}, {0, 0, 0}};
+  static const int off3[6][3] = {{0, 1, 1}, {1, 0, 1}, {1, 1, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int comp = 0; comp < g.ncomp; ++comp) {
+    const int* off = d.dim == 2 ? off2[comp] : off3[comp];
+    unsigned mb = 0;
+    for (int a = 0; a < d.dim; ++a)
+      if (d.bc[a] == KX_PEC && off[a] == 0) mb |= 1u << a;
+    g.maskbits[comp] = mb;
+    g.sighalf[comp] = off[d.layer_axis];
+  }
+  c->n = g.ncomp * ncell;
+  c->esize = d.precision == KX_FP64 ? 8 : 4;
+  c->ld = (c->n + 63) / 64 * 64;
+  c->m = d.krylov_dim;
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(nullptr, KX_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  }
+  const int64_t want = (ncell + NTHREADS - 1) / NTHREADS;
+  c->nblk = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 8));
+
+  const int B = d.batch, m = c->m;
+  const int nla = d.n[d.layer_axis];
+  size_t bytes_V = (size_t)B * (m + 1) * c->ld * c->esize;
+  struct Alloc { void** p; size_t bytes; } allocs[] = {
+      {(void**)&c->d_inv_eps, (size_t)(g.ncomp - g.nh) * ncell * c->esize},
+      {(void**)&c->d_sig2, (size_t)2 * nla * c->esize},
+      {(void**)&c->d_eps_cell, (size_t)ncell * sizeof(double)},
+      {(void**)&c->d_V, bytes_V},
+      {(void**)&c->d_aug, (size_t)B * (m + 1) * 2 * sizeof(double)},
+      {(void**)&c->d_H, (size_t)B * (m + 1) * m * sizeof(double)},
+      {(void**)&c->d_scale, (size_t)B * (m + 2) * sizeof(double)},
+      {(void**)&c->d_part, (size_t)B * (c->nblk + 1) * PST * sizeof(double)},
+      {(void**)&c->d_counter, (size_t)B * 8 * sizeof(unsigned)},
+      {(void**)&c->d_u, (size_t)B * (m + 2) * sizeof(double)},
+      {(void**)&c->d_state, (size_t)B * sizeof(SlotState)},
+      {(void**)&c->d_rho, (size_t)2 * MAXF * sizeof(double)},
+      {(void**)&c->d_coef, (size_t)2 * MAXF * MMAX * sizeof(float)},
+      {(void**)&c->d_coefd, (size_t)2 * MAXF * MMAX * sizeof(double)},
+      {(void**)&c->d_omegas, (size_t)MAXF * sizeof(double)},
+      {(void**)&c->d_small, (size_t)256 * sizeof(double)},
+      {(void**)&c->d_tmp, (size_t)c->n * c->esize},
+      {(void**)&c->d_tmp2, (size_t)c->n * c->esize},
+      {(void**)&c->d_expm_ws, (size_t)(MMAX + 1) * MMAX * MAXF * sizeof(double)},
+      {(void**)&c->d_zre, (size_t)d.max_freqs * c->n * c->esize},
+      {(void**)&c->d_zim, (size_t)d.max_freqs * c->n * c->esize},
+  };
+  for (auto& a : allocs) {
+    e = cudaMalloc(a.p, a.bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      krylov_expm_destroy(c);
+      return fail(nullptr, KX_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+    }
+  }
+  e = cudaMallocHost((void**)&c->h_state, (size_t)B * sizeof(SlotState));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_small, 256 * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    krylov_expm_destroy(c);
+    return fail(nullptr, KX_ENOMEM, "pinned host allocation failed");
+  }
+  e = cudaMemsetAsync(c->d_counter, 0, (size_t)B * 8 * sizeof(unsigned), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_state, 0, (size_t)B * sizeof(SlotState), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_V, 0, bytes_V, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_aug, 0, (size_t)B * (m + 1) * 2 * sizeof(double), c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_eps_cell, eps_cell, (size_t)ncell * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) {
+    krylov_expm_destroy(c);
+    return fail(nullptr, KX_ECUDA, std::string("initialisation failed: ") + cudaGetErrorString(e));
+  }
+  kx_status st = launch_setup_material(c);
+  if (st == KX_OK) {
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) st = KX_ECUDA, c->err = cudaGetErrorString(e);
+  }
+  if (st != KX_OK) {
+    std::string msg = c->err;
+    krylov_expm_destroy(c);
+    return fail(nullptr, st, "material set-up failed: " + msg);
+  }
+  std::memset(&c->stats, 0, sizeof(c->stats));
+  *out = c;
+  return KX_OK;
+}
+
+kx_status krylov_expm_destroy(kx_ctx* c) {
+  if (!c) return KX_OK;
+  cudaStreamSynchronize(c->stream);
+  void* ptrs[] = {c->d_inv_eps, c->d_sig2, c->d_eps_cell, c->d_V, c->d_aug, c->d_H, c->d_scale,
+                  c->d_part, c->d_counter, c->d_u, c->d_state, c->d_rho, c->d_coef, c->d_coefd,
+                  c->d_omegas, c->d_small, c->d_tmp, c->d_tmp2, c->d_expm_ws, c->d_zre, c->d_zim};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_state) cudaFreeHost(c->h_state);
+  if (c->h_small) cudaFreeHost(c->h_small);
+  delete c;
+  return KX_OK;
+}
+
+int64_t kx_num_unknowns(const kx_ctx* c) { return c ? c->n : 0; }
+
+kx_status apply_A(kx_ctx* c, const void* d_v, void* d_w, int transpose) {
+  if (!c) return KX_EINVAL;
+  KX_TRY(check_vec(c, d_v, "d_v"));
+  KX_TRY(check_vec(c, d_w, "d_w"));
+  if (d_v == d_w) return fail(c, KX_EINVAL, "d_v and d_w must not overlap");
+  c->stats.matvecs++;
+  return launch_apply(c, d_v, d_w, transpose ? 1 : 0);
+}
+
+kx_status arnoldi(kx_ctx* c, const void* d_v0, int m, void* d_V, double* H, double* beta,
+                  int* m_done) {
+  if (!c) return KX_EINVAL;
+  KX_TRY(check_vec(c, d_v0, "d_v0"));
+  if (m < 1 || m > c->m) return fail(c, KX_EINVAL, "m out of range 1..krylov_dim");
+  if (!H || !beta || !m_done) return fail(c, KX_EINVAL, "NULL output");
+  const int slot = 0;
+  KX_CUDA(c, cudaMemcpyAsync(slot_col(c, slot, 0), d_v0, c->n * c->esize, cudaMemcpyDeviceToDevice,
+                             c->stream), "copy v0");
+  KX_CUDA(c, cudaMemsetAsync(c->d_H, 0, (size_t)(c->m + 1) * c->m * sizeof(double), c->stream), "zero H");
+  KX_TRY(upload_state(c, slot, fresh_state()));
+  KX_TRY(launch_norm_init(c, slot));
+  SlotState st;
+  KX_TRY(read_state(c, slot, &st));
+  if (!(st.beta > 0.0) || !std::isfinite(st.beta)) return fail(c, KX_ENONFINITE, "v0 is zero or non-finite");
+  KX_TRY(arnoldi_steps(c, slot, m, nullptr));
+  KX_TRY(read_state(c, slot, &st));
+  if (st.status) return fail(c, (kx_status)st.status, "non-finite value in the Arnoldi process");
+  *beta = st.beta;
+  *m_done = st.m_done;
+  // H: context stride c->m + 1 -> caller stride m + 1
+  const bool hdev = is_device_ptr(H);
+  KX_CUDA(c, cudaMemcpy2DAsync(H, (size_t)(m + 1) * sizeof(double), c->d_H,
+                               (size_t)(c->m + 1) * sizeof(double), (size_t)(m + 1) * sizeof(double), m,
+                               hdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+          "H copy");
+  if (d_V) KX_TRY(launch_basis_export(c, slot, d_V, m));
+  return sync(c);
+}
+
+kx_status expm_phi_project(kx_ctx* c, const double* H, int ldh, int m, double beta, double tau,
+                           const double* omegas, int nfreq, double* u_out) {
+  if (!c) return KX_EINVAL;
+  if (!H || !u_out) return fail(c, KX_EINVAL, "NULL argument");
+  if (m < 1 || m > c->m || ldh < m) return fail(c, KX_EINVAL, "bad m or ldh");
+  if (nfreq < 0 || nfreq > c->d.max_freqs) return fail(c, KX_EINVAL, "bad nfreq");
+  if (nfreq > 0) KX_TRY(check_omegas(c, omegas, nfreq));
+  if (!std::isfinite(beta) || !std::isfinite(tau)) return fail(c, KX_ENONFINITE, "non-finite beta or tau");
+  // H -> device workspace with leading dimension m+1 (column-major)
+  double* dH = c->d_expm_ws;
+  const bool hdev = is_device_ptr(H);
+  KX_CUDA(c, cudaMemcpy2DAsync(dH, (size_t)(m + 1) * sizeof(double), H, (size_t)ldh * sizeof(double),
+                               (size_t)m * sizeof(double), m,
+                               hdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+          "H upload");
+  if (nfreq > 0)
+    KX_CUDA(c, cudaMemcpyAsync(c->d_omegas, omegas, sizeof(double) * nfreq, cudaMemcpyHostToDevice,
+                               c->stream), "omega upload");
+  double* du = c->d_expm_ws + (size_t)(m + 1) * m;
+  KX_CUDA(c, cudaMemsetAsync(c->d_small + 64, 0, sizeof(int), c->stream), "status reset");
+  KX_TRY(launch_expm_project(c, dH, m + 1, m, beta, tau, c->d_omegas, nfreq, du));
+  c->stats.expm_evals += nfreq > 0 ? nfreq : 1;
+  const size_t ub = sizeof(double) * (size_t)m * std::max(1, nfreq);
+  const bool udev = is_device_ptr(u_out);
+  KX_CUDA(c, cudaMemcpyAsync(u_out, du, ub, udev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             c->stream), "u copy");
+  int status = 0;
+  KX_CUDA(c, cudaMemcpyAsync(c->h_small, c->d_small + 64, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+          "status read");
+  KX_TRY(sync(c));
+  std::memcpy(&status, c->h_small, sizeof(int));
+  if (status) return fail(c, KX_ENONFINITE, "singular Pade denominator");
+  return KX_OK;
+}
+
+kx_status stationary_solve(kx_ctx* c, const void* d_g, const double* omegas, int nfreq, double rtol,
+                           int max_matvecs, void* d_z_re, void* d_z_im, double* rel_resid, int* matvecs) {
+  if (!c) return KX_EINVAL;
+  KX_TRY(check_vec(c, d_g, "d_g"));
+  KX_TRY(check_vec(c, d_z_re, "d_z_re"));
+  KX_TRY(check_vec(c, d_z_im, "d_z_im"));
+  KX_TRY(check_omegas(c, omegas, nfreq));
+  if (!(rtol > 0.0) || max_matvecs < 1) return fail(c, KX_EINVAL, "rtol must be > 0, max_matvecs >= 1");
+  return stationary_core(c, d_g, omegas, nfreq, rtol, max_matvecs, d_z_re, d_z_im, rel_resid, matvecs);
+}
+
+kx_status expm_action(kx_ctx* c, const void* d_y0, double T, double rtol, void* d_y, double* err_est) {
+  if (!c) return KX_EINVAL;
+  KX_TRY(check_vec(c, d_y0, "d_y0"));
+  KX_TRY(check_vec(c, d_y, "d_y"));
+  if (!(T >= 0.0) || !std::isfinite(T) || !(rtol > 0.0)) return fail(c, KX_EINVAL, "bad T or rtol");
+  const int slot = 0;
+  KX_CUDA(c, cudaMemcpyAsync(slot_col(c, slot, 0), d_y0, c->n * c->esize, cudaMemcpyDeviceToDevice,
+                             c->stream), "copy y0");
+  if (T == 0.0) {
+    KX_CUDA(c, cudaMemcpyAsync(d_y, slot_col(c, slot, 0), c->n * c->esize, cudaMemcpyDeviceToDevice,
+                               c->stream), "copy y");
+    if (err_est) *err_est = 0.0;
+    return sync(c);
+  }
+  SlotState s = fresh_state();
+  s.T = T;
+  s.rtol = rtol;
+  s.tol_mode = 0;
+  KX_TRY(upload_state(c, slot, s));
+  KX_TRY(time_loop(c, slot, nullptr, err_est));
+  KX_CUDA(c, cudaMemcpyAsync(d_y, slot_col(c, slot, 0), c->n * c->esize, cudaMemcpyDeviceToDevice,
+                             c->stream), "copy y");
+  return sync(c);
+}
+
+kx_status response_at_freqs(kx_ctx* c, const void* d_g, const double* omegas, int nfreq, double T,
+                            double rtol, int method, const int* plane, void* d_E_plane,
+                            double* intensity, double* err_est, void* d_Y) {
+  if (!c) return KX_EINVAL;
+  KX_TRY(check_vec(c, d_g, "d_g"));
+  KX_TRY(check_omegas(c, omegas, nfreq));
+  if (!(T > 0.0) || !std::isfinite(T) || !(rtol > 0.0)) return fail(c, KX_EINVAL, "bad T or rtol");
+  if (method != KX_PLAIN && method != KX_SPLIT) return fail(c, KX_EINVAL, "bad method");
+  if (!plane) return fail(c, KX_EINVAL, "plane is NULL");
+  const int axis = plane[0], idx = plane[1];
+  if (axis < 0 || axis >= c->d.dim) return fail(c, KX_EINVAL, "bad plane axis");
+  const int na = axis == 0 ? c->geo.nx : (axis == 1 ? c->geo.ny : c->geo.nz);
+  if (idx < 0 || idx >= na) return fail(c, KX_EINVAL, "bad plane index");
+  int64_t np = 1;
+  for (int a = 0; a < c->d.dim; ++a)
+    if (a != axis) np *= c->d.n[a];
+  const int nE = c->geo.ncomp - c->geo.nh;
+  const int slot = 0;
+  kx_status conv = KX_OK;
+  double* d_int = c->d_small + 128;
+  if (method == KX_SPLIT) {
+    // Fig. alg:spl1, steps 1-3 for every frequency, with all stationary
+    // parts from one shifted solve (Corollary 1 applied to z_stat).
+    kx_status st = stationary_core(c, d_g, omegas, nfreq, rtol * 0.1, 400 * c->m, c->d_zre,
+                                   c->d_zim, nullptr, nullptr);
+    if (st != KX_OK && st != KX_ENOCONV) return st;
+    conv = st;
+  } else {
+    // eta = ||g|| balances the augmented phase entries against the field
+    KX_CUDA(c, cudaMemcpyAsync(slot_col(c, slot, 0), d_g, c->n * c->esize, cudaMemcpyDeviceToDevice,
+                               c->stream), "copy g");
+    KX_TRY(upload_state(c, slot, fresh_state()));
+    KX_TRY(launch_norm_init(c, slot));
+  }
+  SlotState gst;
+  KX_TRY(read_state(c, slot, &gst));
+  const double gnorm = gst.beta;
+  for (int f = 0; f < nfreq; ++f) {
+    SlotState s = fresh_state();
+    s.T = T;
+    s.rtol = rtol;
+    double ef = 0.0;
+    if (method == KX_SPLIT) {
+      // transient y^(T) = exp(-TA) Im z_f  (eq. (y_homo))
+      KX_CUDA(c, cudaMemcpyAsync(slot_col(c, slot, 0), vec_ptr(c, c->d_zim, f), c->n * c->esize,
+                                 cudaMemcpyDeviceToDevice, c->stream), "copy Im z");
+      s.tol_mode = 0;
+      KX_TRY(upload_state(c, slot, s));
+      KX_TRY(time_loop(c, slot, nullptr, &ef));
+    } else {
+      // augmented system x' = -[[A, -g/eta, 0], [0, 0, -W], [0, W, 0]] x,
+      // x(0) = [0; 0; eta]: the two extra entries are eta (sin Wt, cos Wt)
+      KX_CUDA(c, cudaMemsetAsync(slot_col(c, slot, 0), 0, c->n * c->esize, c->stream), "zero y");
+      s.aug = 1;
+      s.omega = omegas[f];
+      s.eta = gnorm > 0.0 ? gnorm : 1.0;
+      s.tol_mode = 1;
+      KX_TRY(upload_state(c, slot, s));
+      KX_TRY(time_loop(c, slot, d_g, &ef));
+    }
+    if (err_est) err_est[f] = ef;
+    void* Ep = d_E_plane ? (char*)d_E_plane + (int64_t)f * nE * np * c->esize : nullptr;
+    void* Yf = d_Y ? vec_ptr(c, d_Y, f) : nullptr;
+    KX_TRY(launch_response(c, f, omegas, T, method == KX_SPLIT, vec_ptr(c, c->d_zre, f),
+                           vec_ptr(c, c->d_zim, f), slot_col(c, slot, 0), axis, idx, Ep, d_int + f, Yf));
+  }
+  if (intensity) {
+    KX_CUDA(c, cudaMemcpyAsync(c->h_small, d_int, sizeof(double) * nfreq, cudaMemcpyDeviceToHost, c->stream),
+            "intensity read");
+    KX_TRY(sync(c));
+    for (int f = 0; f < nfreq; ++f) intensity[f] = c->h_small[f];
+  }
+  KX_TRY(sync(c));
+  if (conv != KX_OK) return fail(c, conv, "stationary solve did not reach its tolerance");
+  return KX_OK;
+}
+
+kx_status kx_get_stats(const kx_ctx* c, kx_stats* out) {
+  if (!c || !out) return KX_EINVAL;
+  *out = c->stats;
+  return KX_OK;
+}
+
+kx_status kx_reset_stats(kx_ctx* c) {
+  if (!c) return KX_EINVAL;
+  std::memset(&c->stats, 0, sizeof(c->stats));
+  return KX_OK;
+}
+
+const char* kx_last_error(const kx_ctx* c) {
+  return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+}  // extern "C"

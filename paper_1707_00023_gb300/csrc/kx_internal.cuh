@@ -1,0 +1,168 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/kx.h"
+
+namespace kx {
+
+constexpr int MMAX = 64;            // largest Krylov dimension
+constexpr int PST = MMAX + 4;       // stride of one block's partial sums
+constexpr int NTHREADS = 256;       // threads per block of the bulk kernels
+constexpr int NWARPS = NTHREADS / 32;
+constexpr int MAXF = 64;            // largest number of frequencies per call
+
+// Geometry of one grid, passed by value to kernels.
+struct Geo {
+  int dim, nx, ny, nz;
+  int64_t ncell;
+  int ncomp, nh;
+  unsigned maskbits[6];  // bit a set: node index 0 along axis a is a wall node
+  int la;                // layer axis
+  int sighalf[6];        // 1 if the component is half-integer along la
+};
+
+// Device-side state of one Krylov basis (one "slot").
+struct SlotState {
+  int done;          // Arnoldi stopped (lucky breakdown)
+  int m_done;        // Arnoldi steps completed in this restart
+  int finished;      // time stepping reached T
+  int status;        // 0 ok, else a kx_status code raised on the device
+  double wmax;       // max ||A v_j|| of this restart (breakdown scale)
+  double beta;       // norm of the current starting vector
+  double t_now;      // time reached
+  double T;          // final time
+  double tau_try;    // trial sub-step length
+  double rtol;       // requested relative accuracy
+  double tol_abs;    // allowed error per unit time (tol_mode 0, set at the first sub-step)
+  double err_acc;    // accumulated error estimate
+  double t_acc;      // last accepted sub-step
+  double omega, eta; // augmented mode: angular frequency and phase scaling
+  int aug;           // 1: state carries [eta sin, eta cos]
+  int tol_mode;      // 0: tolerance from the initial norm; 1: from the current norm
+  int k_acc;
+  int substeps;
+  int expm_evals;
+};
+
+// Pointers of one slot's workspace.
+template <typename T>
+struct Slot {
+  T* V;              // (m+1) columns of ld scalars; stored columns are unnormalised
+  double* aug;       // (m+1) x 2 augmented entries of each column (FP64)
+  double* H;         // (m+1) x m, ldh = m+1, column-major
+  double* scale;     // m+2 column scales: v_i = scale[i] * V_i
+  double* part;      // nblk x PST partial sums
+  unsigned* counter; // block-completion counter (8 slots)
+  double* u;         // projected coefficients (m)
+  SlotState* st;
+};
+
+struct Material {
+  const void* inv_eps;   // (ncomp - nh) x ncell, 1 / mean eps on E nodes
+  const void* sig2;      // sigma at 2*index + half along the layer axis
+};
+
+}  // namespace kx
+
+struct kx_ctx {
+  kx_desc d;
+  cudaStream_t stream;
+  kx::Geo geo;
+  int64_t n;        // unknowns
+  int64_t ld;       // stride between stored basis columns
+  int esize;        // bytes per scalar
+  int m;            // krylov_dim
+  int nblk;         // blocks of the bulk kernels
+  void* d_inv_eps;
+  void* d_sig2;
+  double* d_eps_cell;
+  // per-slot workspace
+  void* d_V;
+  double* d_aug;
+  double* d_H;
+  double* d_scale;
+  double* d_part;
+  unsigned* d_counter;
+  double* d_u;
+  kx::SlotState* d_state;
+  kx::SlotState* h_state;   // pinned host mirror
+  // stationary-solve workspace
+  double* d_rho;            // 2 x MAXF complex residual coefficients
+  float* d_coef;            // 2 x MAXF x MMAX update coefficients (FP32 path)
+  double* d_coefd;          // 2 x MAXF x MMAX update coefficients (FP64 path)
+  double* d_omegas;         // MAXF
+  double* d_small;          // scratch for small host<->device transfers
+  double* h_small;          // pinned
+  void* d_tmp;              // one extra vector
+  void* d_tmp2;             // one extra vector
+  double* d_expm_ws;        // projected exponential workspace
+  void* d_zre;              // stationary parts, max_freqs x n (real)
+  void* d_zim;              // stationary parts, max_freqs x n (imaginary)
+  kx_stats stats;
+  std::string err;
+};
+
+// ---------------------------------------------------------------------------
+// Launch helpers implemented in the .cu files.
+namespace kx {
+
+// stencil.cu
+kx_status launch_setup_material(kx_ctx* c);
+kx_status launch_apply(kx_ctx* c, const void* v, void* w, int transpose);
+kx_status launch_pass_a(kx_ctx* c, int slot, int j, const void* g_aug);
+kx_status launch_pass_b(kx_ctx* c, int slot, int j);
+
+// linalg.cu
+kx_status launch_norm_init(kx_ctx* c, int slot);
+kx_status launch_combine(kx_ctx* c, int slot);
+kx_status launch_basis_export(kx_ctx* c, int slot, void* dV, int m);
+kx_status launch_zupdate(kx_ctx* c, int slot, int nfreq, void* zre, void* zim, int m);
+kx_status launch_true_residual(kx_ctx* c, const void* g, int nfreq, const double* d_om,
+                               void* zre, void* zim, double* out_host);
+kx_status launch_response(kx_ctx* c, int f, const double* h_om, double T, int split,
+                          const void* zre, const void* zim, const void* Y, int plane_axis,
+                          int plane_idx, void* E_plane, double* d_intensity, void* Yout);
+
+// projected.cu
+kx_status launch_substep_control(kx_ctx* c, int slot);
+kx_status launch_expm_project(kx_ctx* c, const double* dH, int ldh, int m, double beta,
+                              double tau, const double* d_om, int nfreq, double* d_u);
+kx_status launch_shifted_solve(kx_ctx* c, int slot, int nfreq, int m);
+
+size_t expm_smem_bytes(int msz);
+
+}  // namespace kx
+
+namespace kx {
+// Workspace pointers of basis slot `slot` of a context.
+template <typename T>
+inline Slot<T> make_slot(kx_ctx* c, int slot) {
+  Slot<T> s;
+  const int m = c->m;
+  s.V = (T*)c->d_V + (int64_t)slot * (m + 1) * c->ld;
+  s.aug = c->d_aug + (int64_t)slot * (m + 1) * 2;
+  s.H = c->d_H + (int64_t)slot * (m + 1) * m;
+  s.scale = c->d_scale + (int64_t)slot * (m + 2);
+  s.part = c->d_part + (int64_t)slot * (c->nblk + 1) * PST;
+  s.counter = c->d_counter + slot * 8;
+  s.u = c->d_u + (int64_t)slot * (m + 2);
+  s.st = c->d_state + slot;
+  return s;
+}
+}  // namespace kx
+
+#define KX_CHECK_LAUNCH(ctx)                                               \
+  do {                                                                     \
+    cudaError_t e__ = cudaGetLastError();                                  \
+    if (e__ != cudaSuccess) {                                              \
+      (ctx)->err = std::string("kernel launch failed: ") +                 \
+                   cudaGetErrorString(e__) + " at " + __FILE__ + ":" +     \
+                   std::to_string(__LINE__);                               \
+      return KX_ECUDA;                                                     \
+    }                                                                      \
+    (ctx)->stats.kernel_launches++;                                        \
+  } while (0)

@@ -1,0 +1,465 @@
+// Bulk vector kernels of the Krylov path: Arnoldi pass B (Gram-Schmidt
+// update and norm), the basis combination y = V_m u, the multi-shift update
+// of the stationary parts, residual norms and the output-plane response.
+// All reductions are deterministic: per-block partials in a fixed order,
+// summed by the last block to finish.
+#include "kx_internal.cuh"
+
+namespace kx {
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_l(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__device__ __forceinline__ bool last_block_l(unsigned* counter) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(counter, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+// Block sum of one double per thread into part[blockIdx.x * PST + slot].
+__device__ __forceinline__ void block_partial(double x, double* part, int slot) {
+  __shared__ double red[NWARPS];
+  x = warp_sum_l(x);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[(int64_t)blockIdx.x * PST + slot] = t;
+  }
+}
+
+__device__ __forceinline__ double grid_total(const double* part, int slot) {
+  double t = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(&part[(int64_t)b * PST + slot]);
+  return t;
+}
+
+template <typename T> struct Vec;
+template <> struct Vec<float> { using t = float4; static constexpr int w = 4; };
+template <> struct Vec<double> { using t = double2; static constexpr int w = 2; };
+
+template <typename T>
+__device__ __forceinline__ void vfma(typename Vec<T>::t& x, T a, const typename Vec<T>::t& y);
+template <>
+__device__ __forceinline__ void vfma<float>(float4& x, float a, const float4& y) {
+  x.x = fmaf(a, y.x, x.x); x.y = fmaf(a, y.y, x.y); x.z = fmaf(a, y.z, x.z); x.w = fmaf(a, y.w, x.w);
+}
+template <>
+__device__ __forceinline__ void vfma<double>(double2& x, double a, const double2& y) {
+  x.x = fma(a, y.x, x.x); x.y = fma(a, y.y, x.y);
+}
+__device__ __forceinline__ float vdot(const float4& a) { return a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w; }
+__device__ __forceinline__ double vdot(const double2& a) { return a.x * a.x + a.y * a.y; }
+template <typename T> __device__ __forceinline__ typename Vec<T>::t vzero();
+template <> __device__ __forceinline__ float4 vzero<float>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <> __device__ __forceinline__ double2 vzero<double>() { return make_double2(0.0, 0.0); }
+
+// ---------------------------------------------------------------------------
+// Arnoldi pass B (step j): w <- w - sum_{i<=j} h_{ij} v_i (classical
+// Gram-Schmidt), h_{j+1,j} = ||w||, scale[j+1] = 1/h_{j+1,j}.  The stored
+// column stays unnormalised (delayed normalisation); a lucky breakdown
+// h_{j+1,j} <= tol * max_i ||A v_i|| stops the process.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_pass_b(Slot<T> s, int j, int64_t n, int64_t ld,
+                                                    int ldh, int aug, double btol) {
+  using V4 = typename Vec<T>::t;
+  constexpr int W = Vec<T>::w;
+  if (s.st->done) return;
+  __shared__ T coef[MMAX + 1];
+  const int ncol = j + 1;
+  for (int q = threadIdx.x; q < ncol; q += blockDim.x)
+    coef[q] = (T)(s.H[q + (int64_t)j * ldh] * s.scale[q]);
+  __syncthreads();
+  T* __restrict__ w = s.V + (int64_t)(j + 1) * ld;
+  double nrm = 0.0;
+  const int64_t nv = n / W;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    V4 x = reinterpret_cast<const V4*>(w)[q];
+    for (int col = 0; col < ncol; ++col) {
+      const V4 v = reinterpret_cast<const V4*>(s.V + (int64_t)col * ld)[q];
+      vfma<T>(x, -coef[col], v);
+    }
+    reinterpret_cast<V4*>(w)[q] = x;
+    nrm += (double)vdot(x);
+  }
+  for (int64_t e = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    T x = w[e];
+    for (int col = 0; col < ncol; ++col) x -= coef[col] * s.V[(int64_t)col * ld + e];
+    w[e] = x;
+    nrm += (double)x * (double)x;
+  }
+  block_partial(nrm, s.part, 0);
+  if (!last_block_l(s.counter)) return;
+  if (threadIdx.x == 0) {
+    *s.counter = 0u;
+    double tot = grid_total(s.part, 0);
+    if (aug) {
+      double a = s.aug[2 * (j + 1)], b = s.aug[2 * (j + 1) + 1];
+      for (int col = 0; col < ncol; ++col) {
+        const double cc = s.H[col + (int64_t)j * ldh] * s.scale[col];
+        a -= cc * s.aug[2 * col];
+        b -= cc * s.aug[2 * col + 1];
+      }
+      s.aug[2 * (j + 1)] = a;
+      s.aug[2 * (j + 1) + 1] = b;
+      tot += a * a + b * b;
+    }
+    const double h = sqrt(tot);
+    s.H[(j + 1) + (int64_t)j * ldh] = h;
+    s.st->m_done = j + 1;
+    if (!isfinite(h)) {
+      s.st->status = KX_ENONFINITE;
+      s.st->done = 1;
+    } else if (h <= btol * s.st->wmax) {
+      s.st->done = 1;            // invariant subspace: the projection is exact
+      s.scale[j + 1] = 0.0;
+    } else {
+      s.scale[j + 1] = 1.0 / h;
+    }
+  }
+}
+
+kx_status launch_pass_b(kx_ctx* c, int slot, int j) {
+  const int ldh = c->m + 1;
+  const int aug = 1;  // augmented entries are zero when unused
+  if (c->d.precision == KX_FP64) {
+    k_pass_b<double><<<c->nblk, NTHREADS, 0, c->stream>>>(make_slot<double>(c, slot), j, c->n, c->ld,
+                                                         ldh, aug, 1e-12);
+  } else {
+    k_pass_b<float><<<c->nblk, NTHREADS, 0, c->stream>>>(make_slot<float>(c, slot), j, c->n, c->ld,
+                                                        ldh, aug, 1e-6);
+  }
+  KX_CHECK_LAUNCH(c);
+  return KX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Start of a restart: beta = ||[V_0; aug_0]||, scale[0] = 1/beta, reset the
+// Arnoldi state.  mode 0: V_0 as it is.  mode 1 (combine): V_0 <- sum_{i<m}
+// u_i scale_i V_i first (the Krylov update y = V_m u, eq. (corr2) /
+// (upd1)); in the augmented case the phase entries are then reset to their
+// exact values eta (sin W t, cos W t).
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_restart(Slot<T> s, int64_t n, int64_t ld, int mode) {
+  using V4 = typename Vec<T>::t;
+  constexpr int W = Vec<T>::w;
+  __shared__ T coef[MMAX];
+  int m = 0;
+  if (mode == 1) {
+    m = s.st->m_done;
+    for (int q = threadIdx.x; q < m; q += blockDim.x) coef[q] = (T)(s.u[q] * s.scale[q]);
+  }
+  __syncthreads();
+  T* __restrict__ y = s.V;
+  double nrm = 0.0;
+  const int64_t nv = n / W;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    V4 x;
+    if (mode == 1) {
+      x = vzero<T>();
+      for (int col = 0; col < m; ++col)
+        vfma<T>(x, coef[col], reinterpret_cast<const V4*>(s.V + (int64_t)col * ld)[q]);
+      reinterpret_cast<V4*>(y)[q] = x;
+    } else {
+      x = reinterpret_cast<const V4*>(y)[q];
+    }
+    nrm += (double)vdot(x);
+  }
+  for (int64_t e = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    T x;
+    if (mode == 1) {
+      x = T(0);
+      for (int col = 0; col < m; ++col) x += coef[col] * s.V[(int64_t)col * ld + e];
+      y[e] = x;
+    } else {
+      x = y[e];
+    }
+    nrm += (double)x * (double)x;
+  }
+  block_partial(nrm, s.part, 0);
+  if (!last_block_l(s.counter)) return;
+  if (threadIdx.x == 0) {
+    *s.counter = 0u;
+    double tot = grid_total(s.part, 0);
+    if (s.st->aug) {
+      const double t = s.st->t_now;
+      s.aug[0] = s.st->eta * sin(s.st->omega * t);
+      s.aug[1] = s.st->eta * cos(s.st->omega * t);
+      tot += s.aug[0] * s.aug[0] + s.aug[1] * s.aug[1];
+    } else {
+      s.aug[0] = 0.0;
+      s.aug[1] = 0.0;
+    }
+    const double b = sqrt(tot);
+    s.st->beta = b;
+    s.scale[0] = b > 0.0 ? 1.0 / b : 0.0;
+    s.st->done = (b > 0.0 && isfinite(b)) ? 0 : 1;
+    if (!isfinite(b)) s.st->status = KX_ENONFINITE;
+    s.st->m_done = 0;
+    s.st->wmax = 0.0;
+  }
+}
+
+template <typename T>
+static kx_status restart_t(kx_ctx* c, int slot, int mode) {
+  k_restart<T><<<c->nblk, NTHREADS, 0, c->stream>>>(make_slot<T>(c, slot), c->n, c->ld, mode);
+  KX_CHECK_LAUNCH(c);
+  return KX_OK;
+}
+
+kx_status launch_norm_init(kx_ctx* c, int slot) {
+  return c->d.precision == KX_FP64 ? restart_t<double>(c, slot, 0) : restart_t<float>(c, slot, 0);
+}
+
+kx_status launch_combine(kx_ctx* c, int slot) {
+  return c->d.precision == KX_FP64 ? restart_t<double>(c, slot, 1) : restart_t<float>(c, slot, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Export the orthonormal basis: dV[:, i] = scale_i V_i (i <= m_done, and the
+// column past a lucky breakdown is zero).
+template <typename T>
+__global__ void k_export(Slot<T> s, T* __restrict__ dV, int64_t n, int64_t ld, int m) {
+  const int md = s.st->m_done;
+  const int brk = s.st->done;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    for (int col = 0; col <= m; ++col) {
+      T x = T(0);
+      if (col < md || (col == md && !brk)) x = (T)(s.scale[col] * (double)s.V[(int64_t)col * ld + e]);
+      dV[(int64_t)col * n + e] = x;
+    }
+  }
+}
+
+kx_status launch_basis_export(kx_ctx* c, int slot, void* dV, int m) {
+  if (c->d.precision == KX_FP64)
+    k_export<double><<<c->nblk, NTHREADS, 0, c->stream>>>(make_slot<double>(c, slot), (double*)dV, c->n, c->ld, m);
+  else
+    k_export<float><<<c->nblk, NTHREADS, 0, c->stream>>>(make_slot<float>(c, slot), (float*)dV, c->n, c->ld, m);
+  KX_CHECK_LAUNCH(c);
+  return KX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Shifted FOM update of every stationary part on one basis:
+//   z_j += V_m c_j,  c_j = rho_j (H_m + i W_j I)^{-1} e_1  (complex),
+// the coefficients (already multiplied by the column scales) in coef:
+//   coef[(2 f) * MMAX + i] real part, coef[(2 f + 1) * MMAX + i] imaginary.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_zupdate(const T* __restrict__ V, int64_t ld, int m,
+                                                     int64_t n, int nfreq, const T* __restrict__ coef,
+                                                     T* __restrict__ zre, T* __restrict__ zim) {
+  extern __shared__ unsigned char smem_raw[];
+  T* cs = reinterpret_cast<T*>(smem_raw);
+  for (int q = threadIdx.x; q < 2 * nfreq * MMAX; q += blockDim.x) cs[q] = coef[q];
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    T v[MMAX];
+#pragma unroll
+    for (int i = 0; i < MMAX; ++i) v[i] = (i < m) ? V[(int64_t)i * ld + e] : T(0);
+    for (int f = 0; f < nfreq; ++f) {
+      const T* cr = cs + (2 * f) * MMAX;
+      const T* ci = cs + (2 * f + 1) * MMAX;
+      T ar = T(0), ai = T(0);
+#pragma unroll
+      for (int i = 0; i < MMAX; ++i) {
+        ar += cr[i] * v[i];
+        ai += ci[i] * v[i];
+      }
+      zre[(int64_t)f * n + e] += ar;
+      zim[(int64_t)f * n + e] += ai;
+    }
+  }
+}
+
+kx_status launch_zupdate(kx_ctx* c, int slot, int nfreq, void* zre, void* zim, int m) {
+  const size_t sm = (size_t)2 * nfreq * MMAX * c->esize;
+  static int attr_done = 0;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_zupdate<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(2 * MAXF * MMAX * sizeof(double)));
+    cudaFuncSetAttribute(k_zupdate<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(2 * MAXF * MMAX * sizeof(float)));
+    attr_done = 1;
+  }
+  if (c->d.precision == KX_FP64) {
+    Slot<double> s = make_slot<double>(c, slot);
+    k_zupdate<double><<<c->nblk, NTHREADS, sm, c->stream>>>(s.V, c->ld, m, c->n, nfreq, c->d_coefd,
+                                                            (double*)zre, (double*)zim);
+  } else {
+    Slot<float> s = make_slot<float>(c, slot);
+    k_zupdate<float><<<c->nblk, NTHREADS, sm, c->stream>>>(s.V, c->ld, m, c->n, nfreq, c->d_coef,
+                                                           (float*)zre, (float*)zim);
+  }
+  KX_CHECK_LAUNCH(c);
+  return KX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ||g - (A + i W) z||^2 / ||g||^2 with Az_re, Az_im already applied:
+//   r_re = g - A z_re + W z_im,   r_im = -(A z_im + W z_re).
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_resid(const T* __restrict__ g, const T* __restrict__ Azr,
+                                                   const T* __restrict__ Azi, const T* __restrict__ zr,
+                                                   const T* __restrict__ zi, double W, int64_t n,
+                                                   double* part, unsigned* counter, double* out) {
+  double rr = 0.0, gg = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double a = (double)g[e] - (double)Azr[e] + W * (double)zi[e];
+    const double b = -((double)Azi[e] + W * (double)zr[e]);
+    rr += a * a + b * b;
+    gg += (double)g[e] * (double)g[e];
+  }
+  block_partial(rr, part, 0);
+  __syncthreads();
+  block_partial(gg, part, 1);
+  if (!last_block_l(counter)) return;
+  if (threadIdx.x == 0) {
+    *counter = 0u;
+    const double R = grid_total(part, 0), G = grid_total(part, 1);
+    *out = G > 0.0 ? sqrt(R / G) : 0.0;
+  }
+}
+
+kx_status launch_true_residual(kx_ctx* c, const void* g, int nfreq, const double* h_om, void* zre,
+                               void* zim, double* out_host) {
+  for (int f = 0; f < nfreq; ++f) {
+    const char* zr = (const char*)zre + (int64_t)f * c->n * c->esize;
+    const char* zi = (const char*)zim + (int64_t)f * c->n * c->esize;
+    kx_status st = launch_apply(c, zr, c->d_tmp, 0);
+    if (st) return st;
+    st = launch_apply(c, zi, c->d_tmp2, 0);
+    if (st) return st;
+    double* part = c->d_part;  // slot 0 partials (not in use during this call)
+    if (c->d.precision == KX_FP64)
+      k_resid<double><<<c->nblk, NTHREADS, 0, c->stream>>>(
+          (const double*)g, (const double*)c->d_tmp, (const double*)c->d_tmp2, (const double*)zr,
+          (const double*)zi, h_om[f], c->n, part, c->d_counter, c->d_small + f);
+    else
+      k_resid<float><<<c->nblk, NTHREADS, 0, c->stream>>>(
+          (const float*)g, (const float*)c->d_tmp, (const float*)c->d_tmp2, (const float*)zr,
+          (const float*)zi, h_om[f], c->n, part, c->d_counter, c->d_small + f);
+    KX_CHECK_LAUNCH(c);
+  }
+  cudaError_t e = cudaMemcpyAsync(c->h_small, c->d_small, sizeof(double) * nfreq,
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    c->err = std::string("residual read-back failed: ") + cudaGetErrorString(e);
+    return KX_ECUDA;
+  }
+  for (int f = 0; f < nfreq; ++f) out_host[f] = c->h_small[f];
+  return KX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Response of one frequency (eq. (split1), final sign '-'):
+//   split: y(T) = sin(W T) Re z + cos(W T) Im z - yhat(T) = Im(e^{iWT} z) - yhat
+//   plain: y(T) = yt (already the full solution)
+// Output plane values (E components) and the summed |E|^2; optionally the
+// full field.
+template <typename T>
+__global__ void k_plane(Geo g, int split, double sW, double cW, const T* __restrict__ zr,
+                        const T* __restrict__ zi, const T* __restrict__ yt, int axis, int idx,
+                        T* __restrict__ E_plane, double* intensity) {
+  const int nE = g.ncomp - g.nh;
+  int na, nb;
+  if (g.dim == 2) {
+    na = axis == 0 ? g.ny : g.nx;
+    nb = 1;
+  } else {
+    na = axis == 0 ? g.ny : g.nx;
+    nb = axis == 2 ? g.ny : g.nz;
+  }
+  const int64_t np = (int64_t)na * nb;
+  double acc = 0.0;
+  for (int64_t t = threadIdx.x; t < nE * np; t += blockDim.x) {
+    const int q = (int)(t / np);
+    const int64_t p = t % np;
+    const int a = (int)(p % na), b = (int)(p / na);
+    int i, j, k;
+    if (g.dim == 2) {
+      k = 0;
+      if (axis == 0) { i = idx; j = a; } else { i = a; j = idx; }
+    } else if (axis == 0) { i = idx; j = a; k = b; }
+    else if (axis == 1) { i = a; j = idx; k = b; }
+    else { i = a; j = b; k = idx; }
+    const int64_t e = (int64_t)(g.nh + q) * g.ncell + ((int64_t)k * g.ny + j) * g.nx + i;
+    double val = (double)yt[e];
+    if (split) val = sW * (double)zr[e] + cW * (double)zi[e] - val;
+    if (E_plane) E_plane[t] = (T)val;
+    acc += val * val;
+  }
+  __shared__ double red[32];
+  acc = warp_sum_l(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    *intensity = s;
+  }
+}
+
+template <typename T>
+__global__ void k_full(int64_t n, int split, double sW, double cW, const T* __restrict__ zr,
+                       const T* __restrict__ zi, const T* __restrict__ yt, T* __restrict__ Y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double val = (double)yt[e];
+    if (split) val = sW * (double)zr[e] + cW * (double)zi[e] - val;
+    Y[e] = (T)val;
+  }
+}
+
+kx_status launch_response(kx_ctx* c, int f, const double* h_om, double T, int split,
+                          const void* zre, const void* zim, const void* yt, int plane_axis,
+                          int plane_idx, void* E_plane, double* d_intensity, void* Yout) {
+  const double W = h_om[f];
+  const double sW = sin(W * T), cW = cos(W * T);
+  if (c->d.precision == KX_FP64) {
+    k_plane<double><<<1, 1024, 0, c->stream>>>(c->geo, split, sW, cW, (const double*)zre,
+                                                (const double*)zim, (const double*)yt, plane_axis,
+                                                plane_idx, (double*)E_plane, d_intensity);
+    KX_CHECK_LAUNCH(c);
+    if (Yout) {
+      k_full<double><<<c->nblk, NTHREADS, 0, c->stream>>>(c->n, split, sW, cW, (const double*)zre,
+                                                          (const double*)zim, (const double*)yt,
+                                                          (double*)Yout);
+      KX_CHECK_LAUNCH(c);
+    }
+  } else {
+    k_plane<float><<<1, 1024, 0, c->stream>>>(c->geo, split, sW, cW, (const float*)zre,
+                                               (const float*)zim, (const float*)yt, plane_axis,
+                                               plane_idx, (float*)E_plane, d_intensity);
+    KX_CHECK_LAUNCH(c);
+    if (Yout) {
+      k_full<float><<<c->nblk, NTHREADS, 0, c->stream>>>(c->n, split, sW, cW, (const float*)zre,
+                                                         (const float*)zim, (const float*)yt,
+                                                         (float*)Yout);
+      KX_CHECK_LAUNCH(c);
+    }
+  }
+  return KX_OK;
+}
+
+}  // namespace kx

@@ -1,0 +1,232 @@
+"""GPU parity: every C-ABI entry point against the FP64 oracle, element by
+element, on seeded inputs that span several thread blocks and a ragged tail.
+
+Tolerances: FP64 path 1e-10 relative L2 (1e-13 for a single operator
+application); FP32 path 1e-6 relative L2 for a single application of A and
+for responses (the accuracy target of the method), looser where a chain of
+FP32 roundings is compared against exact arithmetic (stated per test).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import scenario as S
+from oracle import exact, krylov, yee
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+from paper_1707_00023_gb300 import Context, KxError  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(x, dtype):
+    return torch.tensor(np.asarray(x), dtype=dtype, device="cuda")
+
+
+def random_eps(grid, seed):
+    return 1.0 + 3.0 * np.random.default_rng(seed).random(grid.shape)
+
+
+GRIDS = {
+    # ragged sizes: cell counts are not multiples of the block size
+    "2d_pec": S.Grid(2, (37, 29), (S.PEC, S.PEC), 0, 4, 1.0),
+    "3d_pecz": S.Grid(3, (21, 18, 23), (S.PERIODIC, S.PERIODIC, S.PEC), 2, 3, 1.0),
+    "3d_mixed": S.Grid(3, (16, 12, 10), (S.PEC, S.PERIODIC, S.PERIODIC), 0, 2, 0.5),
+    "2d_periodic_y_layer": S.Grid(2, (19, 33), (S.PERIODIC, S.PEC), 1, 5, 2.0),
+}
+
+
+@pytest.mark.parametrize("name", list(GRIDS))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_apply_A(name, prec, transpose):
+    grid = GRIDS[name]
+    eps = random_eps(grid, 1)
+    op = yee.Operator(grid, eps)
+    ctx = Context(grid, eps, precision=prec, krylov_dim=8)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    for seed in (2, 3):
+        v = S.random_vector(grid.nunk, seed)          # wall entries non-zero: must be ignored
+        vd = dev(v, dt)
+        w = ctx.apply_A(vd, transpose=transpose).cpu().numpy()
+        want = op.apply_T(v) if transpose else op.apply(v)
+        tol = 1e-13 if prec == "fp64" else 1e-6
+        assert rel(w, want) < tol
+        if prec == "fp32":
+            # elementwise: within a few FP32 roundings of the largest term
+            assert np.max(np.abs(w - want)) < 2e-6 * np.max(np.abs(want))
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_arnoldi(prec):
+    grid = GRIDS["3d_pecz"]
+    eps = random_eps(grid, 4)
+    op = yee.Operator(grid, eps)
+    m = 10
+    ctx = Context(grid, eps, precision=prec, krylov_dim=16)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    v0 = S.masked_random_vector(grid, 5)
+    V, H, beta, md = ctx.arnoldi(dev(v0, dt), m)
+    Vo, Ho, bo, mo = krylov.arnoldi(op.apply, v0, m)
+    assert md == m == mo
+    assert abs(beta - bo) < 1e-12 * bo if prec == "fp64" else abs(beta - bo) < 1e-6 * bo
+    Vn = V.cpu().numpy().T
+    if prec == "fp64":
+        assert np.abs(H - Ho).max() < 1e-11 * np.abs(Ho).max()
+        assert np.abs(Vn - Vo).max() < 1e-10
+    else:
+        assert np.abs(H - Ho).max() < 1e-4 * np.abs(Ho).max()
+    # Arnoldi relation with the GPU's own V, H, checked by the oracle operator
+    AV = np.stack([op.apply(Vn[:, i]) for i in range(m)], 1)
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert np.linalg.norm(AV - Vn @ H) < tol * np.linalg.norm(AV)
+    ctx.close()
+
+
+def test_arnoldi_breakdown_invariant_subspace():
+    """A plane wave of a homogeneous, lossless, periodic grid spans an
+    invariant subspace of A of dimension 2: lucky breakdown after 2 steps."""
+    grid = S.Grid(3, (8, 8, 8), (S.PERIODIC,) * 3, 2, 1, 0.0)
+    eps = np.full(grid.shape, 2.25)
+    op = yee.Operator(grid, eps)
+    k = 2 * np.pi * np.array([1, 0, 0]) / 8
+    # Ey polarised wave travelling along x: Ey = cos(k x), Hz from the curl
+    v = np.zeros(grid.nunk)
+    coords = yee.node_coords(grid, 4)
+    v[4 * grid.ncell:5 * grid.ncell] = np.cos(k[0] * coords[0]).reshape(-1)
+    ctx = Context(grid, eps, precision="fp64", krylov_dim=8)
+    V, H, beta, md = ctx.arnoldi(dev(v, torch.float64), 6)
+    assert md == 2
+    Vo, Ho, _, mo = krylov.arnoldi(op.apply, v, 6)
+    assert mo == 2
+    assert np.abs(H[:3, :2] - Ho[:3, :2]).max() < 1e-12
+    ctx.close()
+
+
+@pytest.mark.parametrize("m", [5, 20, 64])
+def test_expm_phi_project(m):
+    rng = np.random.default_rng(m)
+    H = np.triu(rng.standard_normal((m + 1, m)), -1) * 0.3
+    H[np.arange(m), np.arange(m)] += 0.5
+    ctx = Context(GRIDS["2d_pec"], random_eps(GRIDS["2d_pec"], 1), precision="fp64",
+                  krylov_dim=64, max_freqs=4)
+    for tau in (0.01, 1.0, 25.0):
+        u = ctx.expm_phi_project(H, 1.7, tau)
+        want = krylov.proj_exp(H, tau, 1.7)
+        assert rel(u, want) < 1e-11
+    oms = [0.3, 0.9, 2.0]
+    u = ctx.expm_phi_project(H, 1.3, 7.5, oms)
+    for f, om in enumerate(oms):
+        want = krylov.proj_sine(H, 1.3, om, 7.5)
+        assert rel(u[f], want) < 1e-11
+    ctx.close()
+
+
+def test_stationary_solve_fp64():
+    sc = S.config_2d(n=20, ndisks=3)
+    op = yee.Operator(sc.grid, sc.eps_cell)
+    A = op.matrix()
+    oms = S.freq_list(5)
+    ctx = Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=40, max_freqs=8)
+    zr, zi, rr, mv = ctx.stationary_solve(dev(sc.g, torch.float64), oms, rtol=1e-11)
+    assert np.all(rr < 1e-10)
+    for f, om in enumerate(oms):
+        want = exact.z_stat(A, sc.g, om)
+        got = zr[f].cpu().numpy() + 1j * zi[f].cpu().numpy()
+        assert rel(got, want) < 1e-9
+        assert exact.stationary_residual(op.apply, sc.g, om, got) < 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_expm_action(prec):
+    grid = GRIDS["3d_pecz"]
+    eps = random_eps(grid, 6)
+    op = yee.Operator(grid, eps)
+    A = op.matrix()
+    y0 = S.masked_random_vector(grid, 7)
+    T = 12.0
+    want = exact.expm_action(A, T, y0)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    ctx = Context(grid, eps, precision=prec, krylov_dim=30)
+    y, err = ctx.expm_action(dev(y0, dt), T, rtol=1e-11 if prec == "fp64" else 1e-7)
+    tol = 1e-10 if prec == "fp64" else 1e-6
+    assert rel(y.cpu().numpy(), want) < tol
+    ctx.close()
+
+
+@pytest.mark.parametrize("method", ["plain", "split"])
+def test_response_fp64_2d(method):
+    sc = S.config_2d(n=24, ndisks=4, T=30.0)
+    op = yee.Operator(sc.grid, sc.eps_cell)
+    A = op.matrix()
+    oms = S.freq_list(3)
+    ctx = Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=30, max_freqs=4)
+    out = ctx.response_at_freqs(dev(sc.g, torch.float64), oms, sc.T, rtol=1e-11, method=method,
+                                plane=sc.plane, want_full=True)
+    for f, om in enumerate(oms):
+        want = exact.y_plain(A, sc.g, om, sc.T)
+        got = out["Y"][f].cpu().numpy()
+        assert rel(got, want) < 1e-10
+        Pw = yee.plane_fields(sc.grid, want, sc.plane)
+        assert rel(out["E_plane"][f].cpu().numpy(), Pw) < 1e-10
+        assert abs(out["intensity"][f] - (Pw * Pw).sum()) < 1e-9 * (Pw * Pw).sum()
+    ctx.close()
+
+
+@pytest.mark.parametrize("method", ["plain", "split"])
+def test_response_fp32_3d(method):
+    sc = S.config_3d(n=16, fill=0.3, T=40.0)
+    op = yee.Operator(sc.grid, sc.eps_cell)
+    A = op.matrix()
+    oms = S.freq_list(2)
+    ctx = Context(sc.grid, sc.eps_cell, precision="fp32", krylov_dim=32, max_freqs=2)
+    out = ctx.response_at_freqs(dev(sc.g, torch.float32), oms, sc.T, rtol=1e-7, method=method,
+                                plane=sc.plane, want_full=True)
+    for f, om in enumerate(oms):
+        want = exact.y_plain(A, sc.g, om, sc.T)
+        got = out["Y"][f].cpu().numpy()
+        assert rel(got, want) < 1e-6, rel(got, want)
+    ctx.close()
+
+
+def test_zero_source_gives_zero_response():
+    sc = S.config_2d(n=16, ndisks=2, T=10.0)
+    ctx = Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=20, max_freqs=2)
+    g = torch.zeros(sc.grid.nunk, dtype=torch.float64, device="cuda")
+    for method in ("plain", "split"):
+        out = ctx.response_at_freqs(g, S.freq_list(2), 10.0, method=method, plane=sc.plane,
+                                    want_full=True)
+        assert float(out["Y"].abs().max()) == 0.0
+        assert np.all(out["intensity"] == 0.0)
+    ctx.close()
+
+
+def test_invalid_arguments_are_rejected():
+    sc = S.config_2d(n=16, ndisks=2)
+    ctx = Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=20, max_freqs=2)
+    g = torch.tensor(sc.g, dtype=torch.float64, device="cuda")
+    with pytest.raises(KxError):
+        ctx.response_at_freqs(g, S.freq_list(3), 10.0, plane=sc.plane)      # > max_freqs
+    with pytest.raises(KxError):
+        ctx.response_at_freqs(g, [float("nan")], 10.0, plane=sc.plane)
+    with pytest.raises(KxError):
+        ctx.response_at_freqs(g, [0.3], 10.0, plane=(0, 99))
+    with pytest.raises(KxError):
+        ctx.arnoldi(torch.zeros_like(g), 5)
+    bad = S.Grid(2, (16, 16), (S.PEC, S.PEC), 0, 9, 1.0)   # layer thicker than half the grid
+    with pytest.raises(KxError):
+        Context(bad, sc.eps_cell, precision="fp64")
+    eps = sc.eps_cell.copy()
+    eps[3, 3] = float("nan")
+    with pytest.raises(KxError):
+        Context(sc.grid, eps, precision="fp64")
+    ctx.close()
