@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 exponential-Krylov solver: frequency responses/s.
+
+One step = the whole hot path for one batch: the responses y_j(T) of eq.
+(ode) at the workload's frequencies (stationary parts from one shifted
+Krylov solve, transients by time-restarted exponential Krylov, output-plane
+extraction), on seeded synthetic random-scatterer media.
+
+    python bench.py [--gpus N --steps K --warmup W] [--workload NAME] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank solves
+its own replica (independent problems, no data-path collective; weak
+scaling); the barrier and max-over-ranks timing use torch.distributed.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "freq responses/s at 1e-6 rel err vs per-freq Krylov; A·v+GS HBM GB/s"
+
+WORKLOADS = {
+    # 3D Yee 64^3, random eps=2.25 spheres (fill 0.3, r 2-5), 8-cell layer,
+    # Ex plane source, FP32 vectors / FP64 projected, m = 64, T = 400
+    "3d64_m64_T400": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=1,
+                          prec="fp32", method="split", rtol=1e-7, t_oracle=20.0),
+    "3d64_m64_T400_plain": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=1,
+                                prec="fp32", method="plain", rtol=1e-7, t_oracle=20.0),
+    # 2D 64^2, 40 disks, FP64, m = 30, T = 200, plain method
+    "2d64_m30_T200": dict(dim=2, n=64, seed=1708, T=200.0, m=30, nfreq=1, prec="fp64",
+                          method="plain", rtol=1e-11, t_oracle=200.0),
+    # 3D 128^3, 32 frequencies in [0.8, 1.2] Omega0, split
+    "3d128_32f_T400": dict(dim=3, n=128, seed=1710, fill=0.3, T=400.0, m=64, nfreq=32,
+                           prec="fp32", method="split", rtol=1e-7, t_oracle=4.0),
+}
+DEFAULT = "3d64_m64_T400"
+
+
+def scenario_for(w):
+    import scenario as S
+    if w["dim"] == 2:
+        sc = S.config_2d(n=w["n"], seed=w["seed"], T=w["T"], m=w["m"])
+    else:
+        sc = S.config_3d(n=w["n"], seed=w["seed"], fill=w["fill"], T=w["T"], m=w["m"])
+    sc.omegas = S.freq_list(w["nfreq"])
+    return sc
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self, dev_index=0):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                if int(parts[0]) != dev_index:
+                    continue
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        return rank, world, local, dist
+    return 0, 1, 0, None
+
+
+def barrier_max(dist, value):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(w, sc):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    one frequency's exact response over [0, t_oracle] by the augmented
+    route (expm_multiply), scaled to the full interval."""
+    from oracle import exact, yee
+    op = yee.Operator(sc.grid, sc.eps_cell)
+    A = op.matrix()
+    t_s = min(w["t_oracle"], w["T"])
+    t0 = time.perf_counter()
+    exact.y_plain(A, sc.g, float(sc.omegas[0]), t_s)
+    el = time.perf_counter() - t0
+    per_response = el * (w["T"] / t_s)
+    sample = (f"oracle exact response (augmented system, scipy expm_multiply, FP64) of 1 of "
+              f"{w['nfreq']} frequencies over t in [0, {t_s:g}] of [0, {w['T']:g}] on the full "
+              f"{sc.grid.n} grid; {el:.1f} s scaled x{w['T'] / t_s:g}")
+    return 1.0 / per_response, el, sample
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc = scenario_for(w)
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        v, el, sample = oracle_sample(w, sc)
+        vals.append(v)
+    v = float(np.mean(vals[args.warmup:])) if args.steps > 0 else float(vals[-1])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "responses/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * w["nfreq"] / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload},
+            "cpu_baseline": {"kind": "oracle", "value": v, "unit": "responses/s", "cores": 1,
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "responses/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    from paper_1707_00023_gb300 import Context
+
+    rank, world, local, dist = dist_setup(args.gpus)
+    sc = scenario_for(w)
+    dt = torch.float64 if w["prec"] == "fp64" else torch.float32
+    stream = torch.cuda.Stream()
+    ctx = Context(sc.grid, sc.eps_cell, precision=w["prec"], krylov_dim=w["m"],
+                  max_freqs=w["nfreq"], stream=stream)
+    g_host = torch.tensor(sc.g, dtype=dt).pin_memory()
+    g = g_host.to("cuda")
+    torch.cuda.synchronize()
+    oms = sc.omegas
+
+    def step(gv, want_plane=True):
+        with torch.cuda.stream(stream):
+            return ctx.response_at_freqs(gv, oms, w["T"], rtol=w["rtol"], method=w["method"],
+                                         plane=sc.plane, want_plane=want_plane)
+
+    for _ in range(args.warmup):
+        step(g)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, inputs resident in HBM ----------------------
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    clocks.start()
+    launches0 = ctx.stats()["kernel_launches"]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = step(g)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop(local)
+    dev_ms = ev0.elapsed_time(ev1)
+    launches = ctx.stats()["kernel_launches"] - launches0
+    dev_ms = barrier_max(dist, dev_ms)
+    ms_per_step = dev_ms / args.steps
+    responses = w["nfreq"] * args.steps * world
+    value = responses / (dev_ms / 1000.0)
+
+    # ---- end to end through host buffers -------------------------------------
+    nE, npl = ctx.plane_size(sc.plane)
+    host_E = torch.empty((w["nfreq"], nE, npl), dtype=dt).pin_memory()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            gd = g_host.to("cuda", non_blocking=True)
+            out = step(gd)
+            host_E.copy_(out["E_plane"], non_blocking=True)
+        stream.synchronize()
+    e_wall = barrier_max(dist, time.perf_counter() - e0)
+    e2e = {"value": responses / e_wall, "unit": "responses/s",
+           "h2d_bytes_per_step": int(g_host.numel() * g_host.element_size()),
+           "d2h_bytes_per_step": int(host_E.numel() * host_E.element_size() + 8 * w["nfreq"])}
+
+    # ---- roofline of the dominant kernel (untimed pass with event timing) ------
+    ctx.set_timing(True)
+    step(g)
+    kt = ctx.kernel_times()
+    ctx.set_timing(False)
+    total_ms = sum(v["ms"] for v in kt.values())
+    dom = max(("pass_a", "pass_b"), key=lambda k: kt[k]["ms"])
+    peak, peak_kind = peaks()
+    ach = kt[dom]["bytes"] / (kt[dom]["ms"] / 1000.0) / 1e9 if kt[dom]["ms"] > 0 else 0.0
+    ab_bytes = kt["pass_a"]["bytes"] + kt["pass_b"]["bytes"]
+    ab_ms = kt["pass_a"]["ms"] + kt["pass_b"]["ms"]
+    ab_gbs = ab_bytes / (ab_ms / 1000.0) / 1e9 if ab_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": f"k_pass_{dom[-1]}", "achieved": round(ach, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
+                "peak_source": peak_kind,
+                "launches": kt[dom]["launches"], "avg_launch_us": round(1000 * kt[dom]["ms"] / max(1, kt[dom]["launches"]), 2),
+                "share_of_step": round(kt[dom]["ms"] / total_ms, 4) if total_ms else None}
+
+    # ---- accuracy: split vs per-frequency plain Krylov on the GPU (untimed) ---
+    acc = None
+    if w["method"] == "split":
+        with torch.cuda.stream(stream):
+            a = ctx.response_at_freqs(g, oms[:1], w["T"], rtol=w["rtol"], method="split", plane=sc.plane,
+                                      want_plane=True)
+            b = ctx.response_at_freqs(g, oms[:1], w["T"], rtol=w["rtol"], method="plain", plane=sc.plane,
+                                      want_plane=True)
+        stream.synchronize()
+        pa, pb = a["E_plane"][0].double().cpu().numpy(), b["E_plane"][0].double().cpu().numpy()
+        acc = float(np.linalg.norm(pa - pb) / np.linalg.norm(pb))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, el, sample = oracle_sample(w, sc)
+        cpu = {"value": v, "unit": "responses/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "responses/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if w["prec"] == "fp32" else "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "grid": list(sc.grid.n), "unknowns": sc.grid.nunk,
+                           "T": w["T"], "krylov_dim": w["m"], "nfreq": w["nfreq"], "method": w["method"],
+                           "projected": "f64", "parallelism": f"replicas{world}",
+                           "l2": "working set (Krylov basis) larger than L2; no flush"},
+                "roofline": roofline,
+                "arnoldi_hbm_gbs": round(ab_gbs, 1),
+                "kernel_ms_per_step": {k: round(v["ms"], 3) for k, v in kt.items()},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+                "accuracy": {"rel_l2_split_vs_plain": acc}, "wall_s": wall,
+                "stats": ctx.stats()}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

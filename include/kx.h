@@ -181,6 +181,28 @@ kx_status response_at_freqs(kx_ctx* ctx, const void* d_g, const double* omegas,
 kx_status kx_get_stats(const kx_ctx* ctx, kx_stats* out);
 kx_status kx_reset_stats(kx_ctx* ctx);
 
+/* Per-kernel-class device timing (a measurement aid, off by default).
+ * With timing on, every launch of the classes below is bracketed by CUDA
+ * events recorded on the context's stream; kx_kernel_times synchronises the
+ * stream and returns, per class, the summed event time, the algorithmic
+ * bytes those launches must move (the traffic counted in the design notes)
+ * and the launch count, then clears the record.  Timing adds host work per
+ * launch; leave it off in timed runs. */
+enum { KX_K_PASS_A = 0,    /* operator application fused with the Gram-Schmidt dots */
+       KX_K_PASS_B = 1,    /* Gram-Schmidt update and norm                          */
+       KX_K_RESTART = 2,   /* basis combination y = V_m u and renormalisation       */
+       KX_K_PROJ = 3,      /* FP64 projected work (expm, step control, shifted solves) */
+       KX_K_ZUPDATE = 4,   /* multi-shift update of the stationary parts            */
+       KX_K_APPLY = 5,     /* plain operator application                            */
+       KX_NKCLASS = 6 };
+typedef struct {
+  double ms;
+  double bytes;
+  int64_t launches;
+} kx_kernel_time;
+kx_status kx_set_timing(kx_ctx* ctx, int on);
+kx_status kx_kernel_times(kx_ctx* ctx, kx_kernel_time out[KX_NKCLASS]);
+
 /* Text of the last failure on this context ("" if none).  NULL ctx gives
  * the last creation failure of the calling thread. */
 const char* kx_last_error(const kx_ctx* ctx);

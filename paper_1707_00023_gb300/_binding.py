@@ -24,7 +24,9 @@ STATUS_NAMES = {0: "KX_OK", 1: "KX_EINVAL", 2: "KX_ENOMEM", 3: "KX_ECUDA",
 
 EXPORTS = ["krylov_expm_create", "krylov_expm_destroy", "kx_num_unknowns", "apply_A",
            "arnoldi", "expm_phi_project", "stationary_solve", "expm_action",
-           "response_at_freqs", "kx_get_stats", "kx_reset_stats", "kx_last_error"]
+           "response_at_freqs", "kx_get_stats", "kx_reset_stats", "kx_set_timing",
+           "kx_kernel_times", "kx_last_error"]
+KCLASSES = ["pass_a", "pass_b", "restart", "projected", "zupdate", "apply"]
 
 
 class KxError(RuntimeError):
@@ -38,6 +40,10 @@ class Desc(ctypes.Structure):
                 ("layer_axis", ctypes.c_int), ("layer_cells", ctypes.c_int),
                 ("sigma_max", ctypes.c_double), ("precision", ctypes.c_int),
                 ("krylov_dim", ctypes.c_int), ("max_freqs", ctypes.c_int), ("batch", ctypes.c_int)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("bytes", ctypes.c_double), ("launches", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):
@@ -74,6 +80,8 @@ def load_library(path: Optional[str] = None):
                                       ctypes.c_int, ip, vp, dp, dp, vp]
     lib.kx_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.kx_reset_stats.argtypes = [vp]
+    lib.kx_set_timing.argtypes = [vp, ctypes.c_int]
+    lib.kx_kernel_times.argtypes = [vp, ctypes.POINTER(KernelTime)]
     lib.kx_last_error.argtypes = [vp]
     lib.kx_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -164,6 +172,16 @@ class Context:
 
     def reset_stats(self):
         self._check(self.lib.kx_reset_stats(self.h))
+
+    def set_timing(self, on: bool):
+        self._check(self.lib.kx_set_timing(self.h, int(bool(on))))
+
+    def kernel_times(self):
+        """Per-class {ms, bytes, launches} recorded since timing was switched on."""
+        arr = (KernelTime * len(KCLASSES))()
+        self._check(self.lib.kx_kernel_times(self.h, arr))
+        return {k: {"ms": arr[i].ms, "bytes": arr[i].bytes, "launches": arr[i].launches}
+                for i, k in enumerate(KCLASSES)}
 
     # -- ABI calls -----------------------------------------------------------
     def apply_A(self, v, w=None, transpose=False):

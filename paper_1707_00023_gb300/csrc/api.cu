@@ -546,3 +546,54 @@ const char* kx_last_error(const kx_ctx* c) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Per-kernel-class timing.
+namespace kx {
+
+void time_begin(kx_ctx* c) {
+  if (!c->timing) return;
+  cudaEventCreate(&c->pending_a);
+  cudaEventRecord(c->pending_a, c->stream);
+}
+
+void time_end(kx_ctx* c, int cls, double bytes) {
+  if (!c->timing || !c->pending_a) return;
+  cudaEvent_t b;
+  cudaEventCreate(&b);
+  cudaEventRecord(b, c->stream);
+  c->timed.push_back({cls, c->pending_a, b, bytes});
+  c->pending_a = nullptr;
+}
+
+}  // namespace kx
+
+extern "C" {
+
+kx_status kx_set_timing(kx_ctx* c, int on) {
+  if (!c) return KX_EINVAL;
+  c->timing = on ? 1 : 0;
+  return KX_OK;
+}
+
+kx_status kx_kernel_times(kx_ctx* c, kx_kernel_time out[KX_NKCLASS]) {
+  if (!c || !out) return KX_EINVAL;
+  for (int k = 0; k < KX_NKCLASS; ++k) out[k] = {0.0, 0.0, 0};
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
+  for (auto& t : c->timed) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t.a, t.b);
+    if (t.cls >= 0 && t.cls < KX_NKCLASS) {
+      out[t.cls].ms += ms;
+      out[t.cls].bytes += t.bytes;
+      out[t.cls].launches += 1;
+    }
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  c->timed.clear();
+  return KX_OK;
+}
+
+}  // extern "C"

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "../../include/kx.h"
 
@@ -104,6 +105,11 @@ struct kx_ctx {
   void* d_zim;              // stationary parts, max_freqs x n (imaginary)
   kx_stats stats;
   std::string err;
+  // per-kernel-class timing (kx_set_timing)
+  int timing = 0;
+  struct TimedLaunch { int cls; cudaEvent_t a, b; double bytes; };
+  std::vector<TimedLaunch> timed;
+  cudaEvent_t pending_a = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -134,6 +140,10 @@ kx_status launch_expm_project(kx_ctx* c, const double* dH, int ldh, int m, doubl
 kx_status launch_shifted_solve(kx_ctx* c, int slot, int nfreq, int m);
 
 size_t expm_smem_bytes(int msz);
+
+// Timing brackets around one launch (no-ops unless timing is on).
+void time_begin(kx_ctx* c);
+void time_end(kx_ctx* c, int cls, double bytes);
 
 }  // namespace kx
 

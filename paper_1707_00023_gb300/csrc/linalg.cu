@@ -133,9 +133,13 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_b(Slot<T> s, int j, int64_t n
   }
 }
 
+// Algorithmic bytes of pass B at step j: read w and V_0..V_j (j+2 vectors),
+// write the updated column (1).
 kx_status launch_pass_b(kx_ctx* c, int slot, int j) {
   const int ldh = c->m + 1;
   const int aug = 1;  // augmented entries are zero when unused
+  time_begin(c);
+  struct End { kx_ctx* c; int j; ~End() { time_end(c, KX_K_PASS_B, (j + 3.0) * c->n * c->esize); } } end{c, j};
   if (c->d.precision == KX_FP64) {
     k_pass_b<double><<<c->nblk, NTHREADS, 0, c->stream>>>(make_slot<double>(c, slot), j, c->n, c->ld,
                                                          ldh, aug, 1e-12);
@@ -218,7 +222,10 @@ __global__ void __launch_bounds__(NTHREADS) k_restart(Slot<T> s, int64_t n, int6
 
 template <typename T>
 static kx_status restart_t(kx_ctx* c, int slot, int mode) {
+  // bytes: combine reads the m basis columns and writes one; norm reads one
+  time_begin(c);
   k_restart<T><<<c->nblk, NTHREADS, 0, c->stream>>>(make_slot<T>(c, slot), c->n, c->ld, mode);
+  time_end(c, KX_K_RESTART, (mode == 1 ? c->m + 1.0 : 1.0) * c->n * c->esize);
   KX_CHECK_LAUNCH(c);
   return KX_OK;
 }
@@ -300,6 +307,9 @@ kx_status launch_zupdate(kx_ctx* c, int slot, int nfreq, void* zre, void* zim, i
                          (int)(2 * MAXF * MMAX * sizeof(float)));
     attr_done = 1;
   }
+  // bytes: read m basis columns, read and write 2 nfreq stationary vectors
+  time_begin(c);
+  struct End { kx_ctx* c; int m, nf; ~End() { time_end(c, KX_K_ZUPDATE, (m + 4.0 * nf) * c->n * c->esize); } } end{c, m, nfreq};
   if (c->d.precision == KX_FP64) {
     Slot<double> s = make_slot<double>(c, slot);
     k_zupdate<double><<<c->nblk, NTHREADS, sm, c->stream>>>(s.V, c->ld, m, c->n, nfreq, c->d_coefd,

@@ -330,7 +330,9 @@ kx_status launch_substep_control(kx_ctx* c, int slot) {
     attr_done = 1;
   }
   Slot<double> s = make_slot<double>(c, slot);
+  time_begin(c);
   k_substep<<<1, 256, sm, c->stream>>>(s.H, m + 1, s.u, s.st, 32);
+  time_end(c, KX_K_PROJ, 0.0);
   KX_CHECK_LAUNCH(c);
   return KX_OK;
 }
@@ -384,8 +386,10 @@ kx_status launch_expm_project(kx_ctx* c, const double* dH, int ldh, int m, doubl
     attr_done = 1;
   }
   int* status = reinterpret_cast<int*>(c->d_small + 64);
+  time_begin(c);
   k_expm_project<<<nfreq > 0 ? nfreq : 1, 256, expm_smem_bytes(n), c->stream>>>(
       dH, ldh, m, beta, tau, d_om, nfreq, d_u, status);
+  time_end(c, KX_K_PROJ, 0.0);
   KX_CHECK_LAUNCH(c);
   return KX_OK;
 }
@@ -498,6 +502,8 @@ kx_status launch_shifted_solve(kx_ctx* c, int slot, int nfreq, int m) {
     cudaFuncSetAttribute(k_shifted<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(MMAX * MMAX * sizeof(cplx)));
     attr_done = 1;
   }
+  time_begin(c);
+  struct End { kx_ctx* c; ~End() { time_end(c, KX_K_PROJ, 0.0); } } end{c};
   if (c->d.precision == KX_FP64)
     k_shifted<double><<<nfreq, 32, sm, c->stream>>>(s.H, c->m + 1, m, s.scale, c->d_omegas, c->d_rho,
                                                      c->d_coefd, status);

@@ -233,9 +233,14 @@ static kx_status apply_t(kx_ctx* c, const void* v, void* w, int tr) {
   return KX_OK;
 }
 
+// Algorithmic bytes: read v, write w, read 1/eps on the E nodes.
 kx_status launch_apply(kx_ctx* c, const void* v, void* w, int transpose) {
-  return c->d.precision == KX_FP64 ? apply_t<double>(c, v, w, transpose)
-                                   : apply_t<float>(c, v, w, transpose);
+  const double bytes = 2.0 * c->n * c->esize + (double)(c->geo.ncomp - c->geo.nh) * c->geo.ncell * c->esize;
+  time_begin(c);
+  const kx_status st = c->d.precision == KX_FP64 ? apply_t<double>(c, v, w, transpose)
+                                                 : apply_t<float>(c, v, w, transpose);
+  time_end(c, KX_K_APPLY, bytes);
+  return st;
 }
 
 // ---------------------------------------------------------------------------
@@ -400,9 +405,17 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int j, const void* gaug) {
   return KX_OK;
 }
 
+// Algorithmic bytes of pass A at step j: read v_j and V_0..V_{j-1} (j+1
+// vectors), write w (1), read 1/eps on the E nodes, and g when augmented.
 kx_status launch_pass_a(kx_ctx* c, int slot, int j, const void* g_aug) {
-  return c->d.precision == KX_FP64 ? pass_a_t<double>(c, slot, j, g_aug)
-                                   : pass_a_t<float>(c, slot, j, g_aug);
+  const double vb = (double)c->n * c->esize;
+  const double bytes = (j + 2) * vb + (double)(c->geo.ncomp - c->geo.nh) * c->geo.ncell * c->esize +
+                       (g_aug ? vb : 0.0);
+  time_begin(c);
+  const kx_status st = c->d.precision == KX_FP64 ? pass_a_t<double>(c, slot, j, g_aug)
+                                                 : pass_a_t<float>(c, slot, j, g_aug);
+  time_end(c, KX_K_PASS_A, bytes);
+  return st;
 }
 
 }  // namespace kx
