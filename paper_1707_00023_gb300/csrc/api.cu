@@ -258,6 +258,8 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
     return fail(nullptr, KX_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
   }
   const int64_t want = (ncell + NTHREADS - 1) / NTHREADS;
+  c->nsm = nsm;
+  c->ps = nsm * 8;
   c->nblk = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 8));
 
   const int B = d.batch, m = c->m;
@@ -271,7 +273,7 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
       {(void**)&c->d_aug, (size_t)B * (m + 1) * 2 * sizeof(double)},
       {(void**)&c->d_H, (size_t)B * (m + 1) * m * sizeof(double)},
       {(void**)&c->d_scale, (size_t)B * (m + 2) * sizeof(double)},
-      {(void**)&c->d_part, (size_t)B * (c->nblk + 1) * PST * sizeof(double)},
+      {(void**)&c->d_part, (size_t)B * PCOLS * c->ps * sizeof(double)},
       {(void**)&c->d_counter, (size_t)B * 8 * sizeof(unsigned)},
       {(void**)&c->d_u, (size_t)B * (m + 2) * sizeof(double)},
       {(void**)&c->d_state, (size_t)B * sizeof(SlotState)},
@@ -597,3 +599,17 @@ kx_status kx_kernel_times(kx_ctx* c, kx_kernel_time out[KX_NKCLASS]) {
 }
 
 }  // extern "C"
+
+namespace kx {
+
+int persistent_grid(kx_ctx* c, const void* kernel, int64_t rounds, size_t smem) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, NTHREADS, smem) != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  const int64_t cap = std::min<int64_t>((int64_t)c->nsm * occ, c->ps);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(rounds, cap));
+}
+
+}  // namespace kx

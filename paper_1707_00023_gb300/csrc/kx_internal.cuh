@@ -11,7 +11,7 @@
 namespace kx {
 
 constexpr int MMAX = 64;            // largest Krylov dimension
-constexpr int PST = MMAX + 4;       // stride of one block's partial sums
+constexpr int PCOLS = MMAX + 3;     // partial-sum columns per slot
 constexpr int NTHREADS = 256;       // threads per block of the bulk kernels
 constexpr int NWARPS = NTHREADS / 32;
 constexpr int MAXF = 64;            // largest number of frequencies per call
@@ -56,7 +56,8 @@ struct Slot {
   double* aug;       // (m+1) x 2 augmented entries of each column (FP64)
   double* H;         // (m+1) x m, ldh = m+1, column-major
   double* scale;     // m+2 column scales: v_i = scale[i] * V_i
-  double* part;      // nblk x PST partial sums
+  double* part;      // PCOLS x ps partial sums, column-major by block
+  int ps;            // partial-sum column stride (>= any grid size)
   unsigned* counter; // block-completion counter (8 slots)
   double* u;         // projected coefficients (m)
   SlotState* st;
@@ -77,7 +78,9 @@ struct kx_ctx {
   int64_t ld;       // stride between stored basis columns
   int esize;        // bytes per scalar
   int m;            // krylov_dim
-  int nblk;         // blocks of the bulk kernels
+  int nblk;         // blocks of the light bulk kernels
+  int nsm;          // streaming multiprocessors
+  int ps;           // partial-sum column stride = nsm * 8
   void* d_inv_eps;
   void* d_sig2;
   double* d_eps_cell;
@@ -141,6 +144,10 @@ kx_status launch_shifted_solve(kx_ctx* c, int slot, int nfreq, int m);
 
 size_t expm_smem_bytes(int msz);
 
+// Persistent grid for a kernel: resident blocks (occupancy) x SMs, capped
+// by the work and by the partial-sum stride.
+int persistent_grid(kx_ctx* c, const void* kernel, int64_t items_per_block_round, size_t smem);
+
 // Timing brackets around one launch (no-ops unless timing is on).
 void time_begin(kx_ctx* c);
 void time_end(kx_ctx* c, int cls, double bytes);
@@ -157,7 +164,8 @@ inline Slot<T> make_slot(kx_ctx* c, int slot) {
   s.aug = c->d_aug + (int64_t)slot * (m + 1) * 2;
   s.H = c->d_H + (int64_t)slot * (m + 1) * m;
   s.scale = c->d_scale + (int64_t)slot * (m + 2);
-  s.part = c->d_part + (int64_t)slot * (c->nblk + 1) * PST;
+  s.part = c->d_part + (int64_t)slot * PCOLS * c->ps;
+  s.ps = c->ps;
   s.counter = c->d_counter + slot * 8;
   s.u = c->d_u + (int64_t)slot * (m + 2);
   s.st = c->d_state + slot;

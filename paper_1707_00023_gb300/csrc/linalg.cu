@@ -4,47 +4,11 @@
 // All reductions are deterministic: per-block partials in a fixed order,
 // summed by the last block to finish.
 #include "kx_internal.cuh"
+#include "kx_reduce.cuh"
 
 namespace kx {
 
-template <typename T>
-__device__ __forceinline__ T warp_sum_l(T x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
-}
-
-__device__ __forceinline__ bool last_block_l(unsigned* counter) {
-  __shared__ bool am_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned t = atomicAdd(counter, 1u);
-    am_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (am_last) __threadfence();
-  return am_last;
-}
-
-// Block sum of one double per thread into part[blockIdx.x * PST + slot].
-__device__ __forceinline__ void block_partial(double x, double* part, int slot) {
-  __shared__ double red[NWARPS];
-  x = warp_sum_l(x);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    part[(int64_t)blockIdx.x * PST + slot] = t;
-  }
-}
-
-__device__ __forceinline__ double grid_total(const double* part, int slot) {
-  double t = 0.0;
-  for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(&part[(int64_t)b * PST + slot]);
-  return t;
-}
+#define warp_sum_l warp_sum
 
 template <typename T> struct Vec;
 template <> struct Vec<float> { using t = float4; static constexpr int w = 4; };
@@ -62,6 +26,10 @@ __device__ __forceinline__ void vfma<double>(double2& x, double a, const double2
 }
 __device__ __forceinline__ float vdot(const float4& a) { return a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w; }
 __device__ __forceinline__ double vdot(const double2& a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ void vadd_f(float4& x, const float4& y) { x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w; }
+__device__ __forceinline__ void vadd_f(double2& x, const double2& y) { x.x += y.x; x.y += y.y; }
+template <typename T>
+__device__ __forceinline__ void vadd(typename Vec<T>::t& x, const typename Vec<T>::t& y) { vadd_f(x, y); }
 template <typename T> __device__ __forceinline__ typename Vec<T>::t vzero();
 template <> __device__ __forceinline__ float4 vzero<float>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 template <> __device__ __forceinline__ double2 vzero<double>() { return make_double2(0.0, 0.0); }
@@ -85,13 +53,27 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_b(Slot<T> s, int j, int64_t n
   T* __restrict__ w = s.V + (int64_t)(j + 1) * ld;
   double nrm = 0.0;
   const int64_t nv = n / W;
+  const V4* __restrict__ Vv = reinterpret_cast<const V4*>(s.V);
+  const int64_t ldv = ld / W;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
        q += (int64_t)gridDim.x * blockDim.x) {
     V4 x = reinterpret_cast<const V4*>(w)[q];
-    for (int col = 0; col < ncol; ++col) {
-      const V4 v = reinterpret_cast<const V4*>(s.V + (int64_t)col * ld)[q];
-      vfma<T>(x, -coef[col], v);
+    int col = 0;
+    // eight independent column loads in flight per thread
+    for (; col + 8 <= ncol; col += 8) {
+      V4 v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) v[t] = Vv[(int64_t)(col + t) * ldv + q];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) vfma<T>(x, -coef[col + t], v[t]);
     }
+    for (; col + 2 <= ncol; col += 2) {
+      const V4 v0 = Vv[(int64_t)col * ldv + q];
+      const V4 v1 = Vv[(int64_t)(col + 1) * ldv + q];
+      vfma<T>(x, -coef[col], v0);
+      vfma<T>(x, -coef[col + 1], v1);
+    }
+    for (; col < ncol; ++col) vfma<T>(x, -coef[col], Vv[(int64_t)col * ldv + q]);
     reinterpret_cast<V4*>(w)[q] = x;
     nrm += (double)vdot(x);
   }
@@ -102,11 +84,24 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_b(Slot<T> s, int j, int64_t n
     w[e] = x;
     nrm += (double)x * (double)x;
   }
-  block_partial(nrm, s.part, 0);
-  if (!last_block_l(s.counter)) return;
+  block_partial(nrm, s.part, s.ps, 0);
+}
+
+// Finalisation of pass B (one block): h_{j+1,j} = ||w||, scale, breakdown.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_fin_b(Slot<T> s, int j, int ldh, int nb, int aug, double btol) {
+  if (s.st->done) return;
+  const int ncol = j + 1;
+  double x = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) x += __ldcg(s.part + b);
+  __shared__ double red[NWARPS];
+  x = warp_sum(x);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    *s.counter = 0u;
-    double tot = grid_total(s.part, 0);
+    double tot = 0.0;
+#pragma unroll
+    for (int w = 0; w < NWARPS; ++w) tot += red[w];
     if (aug) {
       double a = s.aug[2 * (j + 1)], b = s.aug[2 * (j + 1) + 1];
       for (int col = 0; col < ncol; ++col) {
@@ -140,12 +135,23 @@ kx_status launch_pass_b(kx_ctx* c, int slot, int j) {
   const int aug = 1;  // augmented entries are zero when unused
   time_begin(c);
   struct End { kx_ctx* c; int j; ~End() { time_end(c, KX_K_PASS_B, (j + 3.0) * c->n * c->esize); } } end{c, j};
-  if (c->d.precision == KX_FP64) {
-    k_pass_b<double><<<c->nblk, NTHREADS, 0, c->stream>>>(make_slot<double>(c, slot), j, c->n, c->ld,
-                                                         ldh, aug, 1e-12);
+  static int grid[2] = {0, 0};
+  const int fp64 = c->d.precision == KX_FP64;
+  if (!grid[fp64])
+    grid[fp64] = persistent_grid(c, fp64 ? (const void*)k_pass_b<double> : (const void*)k_pass_b<float>,
+                                 1 << 30, 0);
+  const int64_t rounds = (c->n / (fp64 ? 2 : 4) + NTHREADS - 1) / NTHREADS;
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(rounds, grid[fp64]));
+  if (fp64) {
+    k_pass_b<double><<<nb, NTHREADS, 0, c->stream>>>(make_slot<double>(c, slot), j, c->n, c->ld,
+                                                    ldh, aug, 1e-12);
+    KX_CHECK_LAUNCH(c);
+    k_fin_b<double><<<1, NTHREADS, 0, c->stream>>>(make_slot<double>(c, slot), j, ldh, nb, aug, 1e-12);
   } else {
-    k_pass_b<float><<<c->nblk, NTHREADS, 0, c->stream>>>(make_slot<float>(c, slot), j, c->n, c->ld,
-                                                        ldh, aug, 1e-6);
+    k_pass_b<float><<<nb, NTHREADS, 0, c->stream>>>(make_slot<float>(c, slot), j, c->n, c->ld,
+                                                   ldh, aug, 1e-6);
+    KX_CHECK_LAUNCH(c);
+    k_fin_b<float><<<1, NTHREADS, 0, c->stream>>>(make_slot<float>(c, slot), j, ldh, nb, aug, 1e-6);
   }
   KX_CHECK_LAUNCH(c);
   return KX_OK;
@@ -175,9 +181,23 @@ __global__ void __launch_bounds__(NTHREADS) k_restart(Slot<T> s, int64_t n, int6
        q += (int64_t)gridDim.x * blockDim.x) {
     V4 x;
     if (mode == 1) {
+      const V4* __restrict__ Vv = reinterpret_cast<const V4*>(s.V);
+      const int64_t ldv = ld / W;
+      V4 x1 = vzero<T>();
       x = vzero<T>();
-      for (int col = 0; col < m; ++col)
-        vfma<T>(x, coef[col], reinterpret_cast<const V4*>(s.V + (int64_t)col * ld)[q]);
+      int col = 0;
+      for (; col + 8 <= m; col += 8) {
+        V4 v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = Vv[(int64_t)(col + t) * ldv + q];
+#pragma unroll
+        for (int t = 0; t < 8; t += 2) {
+          vfma<T>(x, coef[col + t], v[t]);
+          vfma<T>(x1, coef[col + t + 1], v[t + 1]);
+        }
+      }
+      for (; col < m; ++col) vfma<T>(x, coef[col], Vv[(int64_t)col * ldv + q]);
+      vadd<T>(x, x1);
       reinterpret_cast<V4*>(y)[q] = x;
     } else {
       x = reinterpret_cast<const V4*>(y)[q];
@@ -196,11 +216,19 @@ __global__ void __launch_bounds__(NTHREADS) k_restart(Slot<T> s, int64_t n, int6
     }
     nrm += (double)x * (double)x;
   }
-  block_partial(nrm, s.part, 0);
-  if (!last_block_l(s.counter)) return;
+  block_partial(nrm, s.part, s.ps, 0);
+  if (!last_block(s.counter)) return;
+  double xs = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) xs += __ldcg(s.part + b);
+  __shared__ double red2[NWARPS];
+  xs = warp_sum(xs);
+  if ((threadIdx.x & 31) == 0) red2[threadIdx.x >> 5] = xs;
+  __syncthreads();
   if (threadIdx.x == 0) {
     *s.counter = 0u;
-    double tot = grid_total(s.part, 0);
+    double tot = 0.0;
+#pragma unroll
+    for (int w = 0; w < NWARPS; ++w) tot += red2[w];
     if (s.st->aug) {
       const double t = s.st->t_now;
       s.aug[0] = s.st->eta * sin(s.st->omega * t);
@@ -330,7 +358,7 @@ template <typename T>
 __global__ void __launch_bounds__(NTHREADS) k_resid(const T* __restrict__ g, const T* __restrict__ Azr,
                                                    const T* __restrict__ Azi, const T* __restrict__ zr,
                                                    const T* __restrict__ zi, double W, int64_t n,
-                                                   double* part, unsigned* counter, double* out) {
+                                                   double* part, int ps, unsigned* counter, double* out) {
   double rr = 0.0, gg = 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -339,13 +367,14 @@ __global__ void __launch_bounds__(NTHREADS) k_resid(const T* __restrict__ g, con
     rr += a * a + b * b;
     gg += (double)g[e] * (double)g[e];
   }
-  block_partial(rr, part, 0);
-  __syncthreads();
-  block_partial(gg, part, 1);
-  if (!last_block_l(counter)) return;
+  block_partial(rr, part, ps, 0);
+  block_partial(gg, part, ps, 1);
+  if (!last_block(counter)) return;
+  __shared__ double tt[2];
+  grid_columns(part, ps, 2, tt);
   if (threadIdx.x == 0) {
     *counter = 0u;
-    const double R = grid_total(part, 0), G = grid_total(part, 1);
+    const double R = tt[0], G = tt[1];
     *out = G > 0.0 ? sqrt(R / G) : 0.0;
   }
 }
@@ -363,11 +392,11 @@ kx_status launch_true_residual(kx_ctx* c, const void* g, int nfreq, const double
     if (c->d.precision == KX_FP64)
       k_resid<double><<<c->nblk, NTHREADS, 0, c->stream>>>(
           (const double*)g, (const double*)c->d_tmp, (const double*)c->d_tmp2, (const double*)zr,
-          (const double*)zi, h_om[f], c->n, part, c->d_counter, c->d_small + f);
+          (const double*)zi, h_om[f], c->n, part, c->ps, c->d_counter, c->d_small + f);
     else
       k_resid<float><<<c->nblk, NTHREADS, 0, c->stream>>>(
           (const float*)g, (const float*)c->d_tmp, (const float*)c->d_tmp2, (const float*)zr,
-          (const float*)zi, h_om[f], c->n, part, c->d_counter, c->d_small + f);
+          (const float*)zi, h_om[f], c->n, part, c->ps, c->d_counter, c->d_small + f);
     KX_CHECK_LAUNCH(c);
   }
   cudaError_t e = cudaMemcpyAsync(c->h_small, c->d_small, sizeof(double) * nfreq,

@@ -8,6 +8,7 @@
 // (all 3 or 6 components of that cell), which keeps the neighbour planes of
 // a block close in time and the reuse inside L1/L2.
 #include "kx_internal.cuh"
+#include "kx_reduce.cuh"
 
 namespace kx {
 
@@ -244,29 +245,6 @@ kx_status launch_apply(kx_ctx* c, const void* v, void* w, int transpose) {
 }
 
 // ---------------------------------------------------------------------------
-// Deterministic grid reduction helpers.
-template <typename T>
-__device__ __forceinline__ T warp_sum(T x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
-}
-
-// Returns true in every thread of the last block to finish.
-__device__ __forceinline__ bool last_block(unsigned* counter) {
-  __shared__ bool am_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned t = atomicAdd(counter, 1u);
-    am_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (am_last) __threadfence();
-  return am_last;
-}
-
-// ---------------------------------------------------------------------------
 // Arnoldi pass A (step j -> column j+1, Sect. 3.2 eq. (Arn)):
 //   w = A v_j  (v_j = scale[j] * V_j)       [augmented: w = [A y - (a/eta) g; -W b; W a]]
 //   d_i = V_i^T w for i <= j, and ||w||^2, fused in one sweep over the cells.
@@ -337,51 +315,220 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_a(Geo g, Slot<T> s, int j, in
     if (lane == 0) acc[warp][MMAX + 1] += (double)nrm;
   }
   __syncthreads();
-  for (int col = threadIdx.x; col < MMAX + 2; col += blockDim.x) {
-    if (col < ncol || col == MMAX + 1) {
-      double t = 0.0;
+  // block partials: columns 0..j are the dots, column j+1 is ||w||^2
+  for (int col = threadIdx.x; col <= ncol; col += blockDim.x) {
+    const int src = col < ncol ? col : MMAX + 1;
+    double t = 0.0;
 #pragma unroll
-      for (int w = 0; w < NWARPS; ++w) t += acc[w][col];
-      s.part[(int64_t)blockIdx.x * PST + col] = t;
-    }
+    for (int w = 0; w < NWARPS; ++w) t += acc[w][src];
+    s.part[(int64_t)col * s.ps + blockIdx.x] = t;
   }
-  if (!last_block(s.counter)) return;
-  __shared__ double tot[MMAX + 2];
-  for (int col = threadIdx.x; col < MMAX + 2; col += blockDim.x) {
-    if (col < ncol || col == MMAX + 1) {
-      double t = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(&s.part[(int64_t)b * PST + col]);
-      tot[col] = t;
+}
+
+// ---------------------------------------------------------------------------
+// Pass A, 3D FP32, four consecutive x-cells per thread (nx % 4 == 0): every
+// field, 1/eps and basis access is one 16-byte load, and the dots of a chunk
+// of 8 basis columns keep 48 such loads in flight per thread.
+__device__ __forceinline__ float4 ld4(const float* __restrict__ p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float f4(const float4& v, int e) { return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w)); }
+__device__ __forceinline__ void set4(float4& v, int e, float x) {
+  if (e == 0) v.x = x; else if (e == 1) v.y = x; else if (e == 2) v.z = x; else v.w = x;
+}
+__device__ __forceinline__ float dot4(const float4& a, const float4& b) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+// zero the elements of a quad that lie on a wall of component c
+__device__ __forceinline__ float4 wall4(const Geo& g, int c, float4 v, int i0, int j, int k) {
+  const unsigned mb = g.maskbits[c];
+  if (((mb & 2u) && j == 0) || ((mb & 4u) && k == 0)) return make_float4(0.f, 0.f, 0.f, 0.f);
+  if ((mb & 1u) && i0 == 0) v.x = 0.f;
+  return v;
+}
+__device__ __forceinline__ float wall1(const Geo& g, int c, float v, int i, int j, int k) {
+  return is_wall(g, c, i, j, k) ? 0.f : v;
+}
+
+template <int AUG>
+__global__ void __launch_bounds__(NTHREADS) k_pass_a4(Geo g, Slot<float> s, int j, int64_t ld,
+                                                     const float* __restrict__ ie,
+                                                     const float* __restrict__ sig2,
+                                                     const float* __restrict__ gsrc) {
+  if (s.st->done) return;
+  __shared__ double acc[NWARPS][MMAX + 2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = threadIdx.x; q < NWARPS * (MMAX + 2); q += blockDim.x) (&acc[0][0])[q] = 0.0;
+  __syncthreads();
+  const double sj = s.scale[j];
+  const float tsj = (float)sj;
+  const float* __restrict__ v = s.V + (int64_t)j * ld;
+  float* __restrict__ wout = s.V + (int64_t)(j + 1) * ld;
+  float gco = 0.f;
+  if (AUG) gco = (float)(-(sj * s.aug[2 * j]) / s.st->eta);
+  const int ncol = j + 1;
+  const int64_t nc = g.ncell;
+  const int64_t nq = nc >> 2;
+  const int64_t nxy = (int64_t)g.nx * g.ny;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nq; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q4 = base + threadIdx.x;
+    const bool act = q4 < nq;
+    float4 o[6];
+    if (act) {
+      const int64_t c0 = q4 << 2;
+      const int i0 = (int)(c0 % g.nx);
+      const int64_t r = c0 / g.nx;
+      const int jj = (int)(r % g.ny), kk = (int)(r / g.ny);
+      const int jp = (jj + 1 == g.ny) ? 0 : jj + 1, jm = (jj == 0) ? g.ny - 1 : jj - 1;
+      const int kp = (kk + 1 == g.nz) ? 0 : kk + 1, km = (kk == 0) ? g.nz - 1 : kk - 1;
+      const int64_t cjp = c0 + (int64_t)(jp - jj) * g.nx, cjm = c0 + (int64_t)(jm - jj) * g.nx;
+      const int64_t ckp = c0 + (int64_t)(kp - kk) * nxy, ckm = c0 + (int64_t)(km - kk) * nxy;
+      const int ixp = (i0 + 4 == g.nx) ? 0 : i0 + 4;     // first element of the next quad
+      const int ixm = (i0 == 0) ? g.nx - 1 : i0 - 1;     // element before the quad
+      const int64_t cxp = c0 - i0 + ixp, cxm = c0 - i0 + ixm;
+      const float4 Hx = wall4(g, 0, ld4(v + c0), i0, jj, kk);
+      const float4 Hy = wall4(g, 1, ld4(v + nc + c0), i0, jj, kk);
+      const float4 Hz = wall4(g, 2, ld4(v + 2 * nc + c0), i0, jj, kk);
+      const float4 Ex = wall4(g, 3, ld4(v + 3 * nc + c0), i0, jj, kk);
+      const float4 Ey = wall4(g, 4, ld4(v + 4 * nc + c0), i0, jj, kk);
+      const float4 Ez = wall4(g, 5, ld4(v + 5 * nc + c0), i0, jj, kk);
+      const float4 Ez_jp = wall4(g, 5, ld4(v + 5 * nc + cjp), i0, jp, kk);
+      const float4 Ex_jp = wall4(g, 3, ld4(v + 3 * nc + cjp), i0, jp, kk);
+      const float4 Ey_kp = wall4(g, 4, ld4(v + 4 * nc + ckp), i0, jj, kp);
+      const float4 Ex_kp = wall4(g, 3, ld4(v + 3 * nc + ckp), i0, jj, kp);
+      const float4 Hz_jm = wall4(g, 2, ld4(v + 2 * nc + cjm), i0, jm, kk);
+      const float4 Hx_jm = wall4(g, 0, ld4(v + cjm), i0, jm, kk);
+      const float4 Hy_km = wall4(g, 1, ld4(v + nc + ckm), i0, jj, km);
+      const float4 Hx_km = wall4(g, 0, ld4(v + ckm), i0, jj, km);
+      const float Ez_n = wall1(g, 5, v[5 * nc + cxp], ixp, jj, kk);
+      const float Ey_n = wall1(g, 4, v[4 * nc + cxp], ixp, jj, kk);
+      const float Hz_p = wall1(g, 2, v[2 * nc + cxm], ixm, jj, kk);
+      const float Hy_p = wall1(g, 1, v[nc + cxm], ixm, jj, kk);
+      const float4 ie0 = ld4(ie + c0), ie1 = ld4(ie + nc + c0), ie2 = ld4(ie + 2 * nc + c0);
+      float4 g4[6];
+      if (AUG) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) g4[c] = wall4(g, c, ld4(gsrc + c * nc + c0), i0, jj, kk);
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = i0 + e;
+        const int li = g.la == 0 ? i : (g.la == 1 ? jj : kk);
+        float sg[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sg[c] = sig2[2 * li + g.sighalf[c]];
+        const float ez = f4(Ez, e), ey = f4(Ey, e), ex = f4(Ex, e);
+        const float hx = f4(Hx, e), hy = f4(Hy, e), hz = f4(Hz, e);
+        const float ez_ip = e < 3 ? f4(Ez, e + 1) : Ez_n;
+        const float ey_ip = e < 3 ? f4(Ey, e + 1) : Ey_n;
+        const float hz_im = e > 0 ? f4(Hz, e - 1) : Hz_p;
+        const float hy_im = e > 0 ? f4(Hy, e - 1) : Hy_p;
+        const float cHx = (hz - f4(Hz_jm, e)) - (hy - f4(Hy_km, e));
+        const float cHy = (hx - f4(Hx_km, e)) - (hz - hz_im);
+        const float cHz = (hy - hy_im) - (hx - f4(Hx_jm, e));
+        float out[6];
+        out[0] = sg[0] * hx + ((f4(Ez_jp, e) - ez) - (f4(Ey_kp, e) - ey));
+        out[1] = sg[1] * hy + ((f4(Ex_kp, e) - ex) - (ez_ip - ez));
+        out[2] = sg[2] * hz + ((ey_ip - ey) - (f4(Ex_jp, e) - ex));
+        out[3] = f4(ie0, e) * (sg[3] * ex - cHx);
+        out[4] = f4(ie1, e) * (sg[4] * ey - cHy);
+        out[5] = f4(ie2, e) * (sg[5] * ez - cHz);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          float x = is_wall(g, c, i, jj, kk) ? 0.f : out[c] * tsj;
+          if (AUG) x += gco * f4(g4[c], e);
+          set4(o[c], e, x);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) *reinterpret_cast<float4*>(wout + c * nc + c0) = o[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) o[c] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    float nrm = 0.f;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) nrm += dot4(o[c], o[c]);
+    const int64_t c0 = act ? (q4 << 2) : 0;
+    for (int cb = 0; cb < ncol; cb += 8) {
+      float p[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        p[t] = 0.f;
+        const int col = cb + t;
+        if (act && col < ncol) {
+          const float* __restrict__ vc = s.V + (int64_t)col * ld + c0;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) p[t] += dot4(ld4(vc + c * nc), o[c]);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) p[t] = warp_sum(p[t]);
+      if (lane < 8 && cb + lane < ncol) {
+        float mine = p[0];
+#pragma unroll
+        for (int t = 1; t < 8; ++t) if (lane == t) mine = p[t];
+        acc[warp][cb + lane] += (double)mine;
+      }
+    }
+    nrm = warp_sum(nrm);
+    if (lane == 0) acc[warp][MMAX + 1] += (double)nrm;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    *s.counter = 0u;
-    double nrm2 = tot[MMAX + 1];
-    if (AUG) {
-      // augmented entries of w = scale_j * [-W b_j, W a_j]
-      const double W = s.st->omega;
-      const double wa = -W * sj * s.aug[2 * j + 1];
-      const double wb = W * sj * s.aug[2 * j];
-      s.aug[2 * (j + 1)] = wa;
-      s.aug[2 * (j + 1) + 1] = wb;
-      for (int col = 0; col < ncol; ++col)
-        tot[col] += s.aug[2 * col] * wa + s.aug[2 * col + 1] * wb;
-      nrm2 += wa * wa + wb * wb;
+  for (int col = threadIdx.x; col <= ncol; col += blockDim.x) {
+    const int src = col < ncol ? col : MMAX + 1;
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < NWARPS; ++w) t += acc[w][src];
+    s.part[(int64_t)col * s.ps + blockIdx.x] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Finalisation of pass A, one block per column c <= j+1: sum the block
+// partials of column c in a fixed order; columns c <= j give
+// H[c, j] = scale[c] * d_c (plus the augmented entries' share), column j+1
+// gives ||w|| (breakdown scale) and the augmented entries of w.
+__global__ void __launch_bounds__(NTHREADS) k_fin_a(Slot<float> sf, Slot<double> sd, int dbl, int j, int ldh,
+                                                   int nb, int aug) {
+  double* part = dbl ? sd.part : sf.part;
+  const int ps = dbl ? sd.ps : sf.ps;
+  double* H = dbl ? sd.H : sf.H;
+  double* scale = dbl ? sd.scale : sf.scale;
+  double* augv = dbl ? sd.aug : sf.aug;
+  SlotState* st = dbl ? sd.st : sf.st;
+  if (st->done) return;
+  const int col = blockIdx.x;
+  const int ncol = j + 1;
+  double x = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) x += __ldcg(part + (int64_t)col * ps + b);
+  __shared__ double red[NWARPS];
+  x = warp_sum(x);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double tot = 0.0;
+#pragma unroll
+  for (int w = 0; w < NWARPS; ++w) tot += red[w];
+  const double sj = scale[j];
+  double wa = 0.0, wb = 0.0;
+  if (aug) {
+    const double W = st->omega;
+    wa = -W * sj * augv[2 * j + 1];
+    wb = W * sj * augv[2 * j];
+  }
+  if (col < ncol) {
+    if (aug) tot += augv[2 * col] * wa + augv[2 * col + 1] * wb;
+    const double h = scale[col] * tot;
+    H[col + (int64_t)j * ldh] = h;
+    if (!isfinite(h)) { st->status = KX_ENONFINITE; st->done = 1; }
+  } else {
+    if (aug) {
+      augv[2 * (j + 1)] = wa;
+      augv[2 * (j + 1) + 1] = wb;
+      tot += wa * wa + wb * wb;
     }
-    bool finite = isfinite(nrm2);
-    for (int col = 0; col < ncol; ++col) {
-      const double h = s.scale[col] * tot[col];
-      finite = finite && isfinite(h);
-      s.H[col + (int64_t)j * ldh] = h;
-    }
-    const double wn = sqrt(nrm2);
-    if (wn > s.st->wmax) s.st->wmax = wn;
-    s.part[(int64_t)gridDim.x * PST] = nrm2;  // ||w||^2 for pass B
-    if (!finite) {
-      s.st->status = KX_ENONFINITE;
-      s.st->done = 1;
-    }
+    const double wn = sqrt(tot);
+    if (!isfinite(wn)) { st->status = KX_ENONFINITE; st->done = 1; }
+    if (wn > st->wmax) st->wmax = wn;
   }
 }
 
@@ -394,13 +541,39 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int j, const void* gaug) {
   const T* sg = (const T*)c->d_sig2;
   const T* gs = (const T*)gaug;
   const int ldh = m + 1;
-  if (g.dim == 2) {
-    if (gaug) k_pass_a<T, 2, 1><<<c->nblk, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, ldh, ie, sg, gs);
-    else k_pass_a<T, 2, 0><<<c->nblk, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, ldh, ie, sg, gs);
-  } else {
-    if (gaug) k_pass_a<T, 3, 1><<<c->nblk, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, ldh, ie, sg, gs);
-    else k_pass_a<T, 3, 0><<<c->nblk, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, ldh, ie, sg, gs);
+  // the quad kernel needs 16-byte aligned rows of every array it reads
+  const bool vec4 = sizeof(T) == 4 && g.dim == 3 && (g.nx % 4) == 0 &&
+                    ((uintptr_t)gaug % 16) == 0;
+  const int64_t items = vec4 ? g.ncell / 4 : g.ncell;
+  const int64_t rounds = (items + NTHREADS - 1) / NTHREADS;
+  static int grid[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  const int kind = vec4 ? 2 : (g.dim == 3);
+  int& gr = grid[kind][gaug != nullptr];
+  if (!gr) {
+    const void* fn;
+    if (vec4) fn = gaug ? (const void*)k_pass_a4<1> : (const void*)k_pass_a4<0>;
+    else if (g.dim == 2) fn = gaug ? (const void*)k_pass_a<T, 2, 1> : (const void*)k_pass_a<T, 2, 0>;
+    else fn = gaug ? (const void*)k_pass_a<T, 3, 1> : (const void*)k_pass_a<T, 3, 0>;
+    gr = persistent_grid(c, fn, 1 << 30, 0);
   }
+  const int nb = (int)std::min<int64_t>(rounds, gr);
+  if (vec4) {
+    Slot<float> sf = make_slot<float>(c, slot);
+    const float* ief = (const float*)c->d_inv_eps;
+    const float* sgf = (const float*)c->d_sig2;
+    if (gaug) k_pass_a4<1><<<nb, NTHREADS, 0, c->stream>>>(g, sf, j, c->ld, ief, sgf, (const float*)gaug);
+    else k_pass_a4<0><<<nb, NTHREADS, 0, c->stream>>>(g, sf, j, c->ld, ief, sgf, nullptr);
+  } else if (g.dim == 2) {
+    if (gaug) k_pass_a<T, 2, 1><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, ldh, ie, sg, gs);
+    else k_pass_a<T, 2, 0><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, ldh, ie, sg, gs);
+  } else {
+    if (gaug) k_pass_a<T, 3, 1><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, ldh, ie, sg, gs);
+    else k_pass_a<T, 3, 0><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, ldh, ie, sg, gs);
+  }
+  KX_CHECK_LAUNCH(c);
+  const int dbl = sizeof(T) == 8;
+  k_fin_a<<<j + 2, NTHREADS, 0, c->stream>>>(make_slot<float>(c, slot), make_slot<double>(c, slot), dbl, j,
+                                             ldh, nb, gaug != nullptr);
   KX_CHECK_LAUNCH(c);
   return KX_OK;
 }
