@@ -207,6 +207,41 @@ kx_status kx_kernel_times(kx_ctx* ctx, kx_kernel_time out[KX_NKCLASS]);
  * the last creation failure of the calling thread. */
 const char* kx_last_error(const kx_ctx* ctx);
 
+/* Allocation-free Arnoldi (the paper has no counterpart: this is a
+ * deployment convenience).  Some callers cannot allocate device memory at
+ * all -- code running inside another runtime's memory pool or a captured
+ * graph, plug-ins handed a fixed arena, services that forbid cudaMalloc and
+ * cudaFree after start-up -- and so cannot create a context.  This call needs
+ * no context and performs no device allocation: the caller passes every
+ * input and output, the basis array d_V doubles as the Krylov workspace, and
+ * the remaining scratch (block partial sums, column scales, the step state
+ * and a completion counter) lives in one fixed device array of
+ * KX_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the
+ * library holds until the process exits.
+ *   desc      : grid, boundaries, layer and precision as for
+ *               krylov_expm_create (krylov_dim, max_freqs, batch ignored).
+ *   d_eps_cell: DEVICE array of the per-cell permittivities (double).
+ *   d_v0      : device start vector, n scalars (not modified).
+ *   m         : 1 .. 64 Arnoldi steps; larger m is rejected (KX_EINVAL),
+ *               the scratch array holds at most 64 columns.
+ *   d_V       : device n x (m+1) basis (leading dim n), 16-byte aligned,
+ *               with n * sizeof(scalar) a multiple of 16 (KX_EINVAL
+ *               otherwise); returned orthonormal as by arnoldi().
+ *   d_H       : device (m+1) x m FP64 Hessenberg matrix (column-major).
+ *   beta, m_done: host outputs as for arnoldi().
+ * Results match arnoldi() on a context with the same descriptor.  The call
+ * synchronises cuda_stream.  Its first call on a device takes the device
+ * address of the scratch array (set-up), so make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents (each call clears what must start at zero); calls whose GPU work
+ * overlaps, on different streams or from unsynchronised host threads, race
+ * on it.  Errors are reported by kx_noalloc_last_error(). */
+#define KX_NOALLOC_SCRATCH_BYTES (1310720)
+kx_status kx_arnoldi_noalloc(const kx_desc* desc, const double* d_eps_cell, const void* d_v0,
+                             int m, void* d_V, double* d_H, double* beta, int* m_done,
+                             void* cuda_stream);
+const char* kx_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

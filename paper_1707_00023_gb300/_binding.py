@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "KX_OK", 1: "KX_EINVAL", 2: "KX_ENOMEM", 3: "KX_ECUDA",
 EXPORTS = ["krylov_expm_create", "krylov_expm_destroy", "kx_num_unknowns", "apply_A",
            "arnoldi", "expm_phi_project", "stationary_solve", "expm_action",
            "response_at_freqs", "kx_get_stats", "kx_reset_stats", "kx_set_timing",
-           "kx_kernel_times", "kx_last_error"]
+           "kx_kernel_times", "kx_last_error", "kx_arnoldi_noalloc", "kx_noalloc_last_error"]
 KCLASSES = ["pass_a", "pass_b", "restart", "projected", "zupdate", "apply"]
 
 
@@ -84,8 +84,11 @@ def load_library(path: Optional[str] = None):
     lib.kx_kernel_times.argtypes = [vp, ctypes.POINTER(KernelTime)]
     lib.kx_last_error.argtypes = [vp]
     lib.kx_last_error.restype = ctypes.c_char_p
+    lib.kx_arnoldi_noalloc.argtypes = [ctypes.POINTER(Desc), vp, vp, ctypes.c_int, vp, vp, dp, ip, vp]
+    lib.kx_noalloc_last_error.argtypes = []
+    lib.kx_noalloc_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name != "kx_num_unknowns" and name != "kx_last_error":
+        if name not in ("kx_num_unknowns", "kx_last_error", "kx_noalloc_last_error"):
             getattr(lib, name).restype = ctypes.c_int
     if path is None:
         _lib = lib

@@ -16,7 +16,7 @@ namespace {
 thread_local std::string g_create_err;
 
 kx_status fail(kx_ctx* c, kx_status code, const std::string& msg) {
-  if (c) c->err = msg;
+  if (c) snprintf(c->err, sizeof(c->err), "%s", msg.c_str());
   else g_create_err = msg;
   return code;
 }
@@ -316,7 +316,7 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
   kx_status st = launch_setup_material(c);
   if (st == KX_OK) {
     e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) st = KX_ECUDA, c->err = cudaGetErrorString(e);
+    if (e != cudaSuccess) st = KX_ECUDA, snprintf(c->err, sizeof(c->err), "%s", cudaGetErrorString(e));
   }
   if (st != KX_OK) {
     std::string msg = c->err;
@@ -544,7 +544,7 @@ kx_status kx_reset_stats(kx_ctx* c) {
 }
 
 const char* kx_last_error(const kx_ctx* c) {
-  return c ? c->err.c_str() : g_create_err.c_str();
+  return c ? c->err : g_create_err.c_str();
 }
 
 }  // extern "C"

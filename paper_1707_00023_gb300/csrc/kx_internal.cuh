@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <cstdio>
 #include <string>
 #include <vector>
 
@@ -107,7 +108,7 @@ struct kx_ctx {
   void* d_zre;              // stationary parts, max_freqs x n (real)
   void* d_zim;              // stationary parts, max_freqs x n (imaginary)
   kx_stats stats;
-  std::string err;
+  char err[512] = {0};   // fixed buffer: recording an error allocates nothing
   // per-kernel-class timing (kx_set_timing)
   int timing = 0;
   struct TimedLaunch { int cls; cudaEvent_t a, b; double bytes; };
@@ -123,6 +124,8 @@ namespace kx {
 kx_status launch_setup_material(kx_ctx* c);
 kx_status launch_apply(kx_ctx* c, const void* v, void* w, int transpose);
 kx_status launch_pass_a(kx_ctx* c, int slot, int j, const void* g_aug);
+// pass A reading the per-cell permittivity directly (no 1/eps table)
+kx_status launch_pass_a_cells(kx_ctx* c, int slot, int j, const double* d_eps_cell);
 kx_status launch_pass_b(kx_ctx* c, int slot, int j);
 
 // linalg.cu
@@ -173,14 +176,13 @@ inline Slot<T> make_slot(kx_ctx* c, int slot) {
 }
 }  // namespace kx
 
-#define KX_CHECK_LAUNCH(ctx)                                               \
-  do {                                                                     \
-    cudaError_t e__ = cudaGetLastError();                                  \
-    if (e__ != cudaSuccess) {                                              \
-      (ctx)->err = std::string("kernel launch failed: ") +                 \
-                   cudaGetErrorString(e__) + " at " + __FILE__ + ":" +     \
-                   std::to_string(__LINE__);                               \
-      return KX_ECUDA;                                                     \
-    }                                                                      \
-    (ctx)->stats.kernel_launches++;                                        \
+#define KX_CHECK_LAUNCH(ctx)                                                        \
+  do {                                                                              \
+    cudaError_t e__ = cudaGetLastError();                                           \
+    if (e__ != cudaSuccess) {                                                       \
+      snprintf((ctx)->err, sizeof((ctx)->err), "kernel launch failed: %s at %s:%d", \
+               cudaGetErrorString(e__), __FILE__, __LINE__);                        \
+      return KX_ECUDA;                                                              \
+    }                                                                               \
+    (ctx)->stats.kernel_launches++;                                                 \
   } while (0)

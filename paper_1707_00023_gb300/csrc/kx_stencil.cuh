@@ -1,0 +1,182 @@
+// Yee-grid stencil of the operator A (eq. (ode)) shared by the kernels.
+#pragma once
+
+#include "kx_internal.cuh"
+
+namespace kx {
+
+__device__ __forceinline__ bool is_wall(const Geo& g, int c, int i, int j, int k) {
+  const unsigned mb = g.maskbits[c];
+  return ((mb & 1u) && i == 0) || ((mb & 2u) && j == 0) || ((mb & 4u) && k == 0);
+}
+
+struct Cell {
+  int i, j, k, ip, im, jp, jm, kp, km;
+  int64_t c0, cip, cim, cjp, cjm, ckp, ckm;
+};
+
+__device__ __forceinline__ Cell make_cell(const Geo& g, int64_t cell) {
+  Cell q;
+  q.i = (int)(cell % g.nx);
+  const int64_t r = cell / g.nx;
+  q.j = (int)(r % g.ny);
+  q.k = (int)(r / g.ny);
+  q.ip = (q.i + 1 == g.nx) ? 0 : q.i + 1;
+  q.im = (q.i == 0) ? g.nx - 1 : q.i - 1;
+  q.jp = (q.j + 1 == g.ny) ? 0 : q.j + 1;
+  q.jm = (q.j == 0) ? g.ny - 1 : q.j - 1;
+  q.c0 = cell;
+  q.cip = cell + (q.ip - q.i);
+  q.cim = cell + (q.im - q.i);
+  q.cjp = cell + (int64_t)(q.jp - q.j) * g.nx;
+  q.cjm = cell + (int64_t)(q.jm - q.j) * g.nx;
+  if (g.dim == 3) {
+    const int64_t nxy = (int64_t)g.nx * g.ny;
+    q.kp = (q.k + 1 == g.nz) ? 0 : q.k + 1;
+    q.km = (q.k == 0) ? g.nz - 1 : q.k - 1;
+    q.ckp = cell + (int64_t)(q.kp - q.k) * nxy;
+    q.ckm = cell + (int64_t)(q.km - q.k) * nxy;
+  } else {
+    q.kp = q.km = 0;
+    q.ckp = q.ckm = cell;
+  }
+  return q;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldv(const Geo& g, const T* __restrict__ v, int c, int64_t idx, int i,
+                                 int j, int k) {
+  return is_wall(g, c, i, j, k) ? T(0) : v[(int64_t)c * g.ncell + idx];
+}
+
+// Material accessors.  TableMat reads the 1/eps arrays and the sigma table
+// built at context creation; CellMat derives both from the per-cell
+// permittivity and the layer parameters on the fly (no precomputed arrays).
+template <typename T>
+struct TableMat {
+  const T* __restrict__ ie;     // (ncomp - nh) x ncell
+  const T* __restrict__ sig2;   // sigma at 2 * index + half along the layer axis
+  __device__ __forceinline__ T inv_eps(const Geo& g, int e, int64_t idx) const {
+    return ie[(int64_t)e * g.ncell + idx];
+  }
+  __device__ __forceinline__ T sigma(const Geo& g, const Cell& q, int c) const {
+    const int li = g.la == 0 ? q.i : (g.la == 1 ? q.j : q.k);
+    return sig2[2 * li + g.sighalf[c]];
+  }
+};
+
+template <typename T>
+struct CellMat {
+  const double* __restrict__ eps;  // ncell, x fastest
+  double smax;
+  int L;
+  // 1 / (mean permittivity of the cells whose closure holds E node e of cell idx)
+  __device__ __forceinline__ T inv_eps(const Geo& g, int e, int64_t idx) const {
+    const int i = (int)(idx % g.nx);
+    const int64_t r = idx / g.nx;
+    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    const int im = i == 0 ? g.nx - 1 : i - 1, jm = j == 0 ? g.ny - 1 : j - 1;
+    const int km = k == 0 ? g.nz - 1 : k - 1;
+    const int64_t nx = g.nx, nxy = (int64_t)g.nx * g.ny;
+    double s;
+    if (g.dim == 2) {
+      s = eps[j * nx + i] + eps[j * nx + im] + eps[jm * nx + i] + eps[jm * nx + im];
+    } else if (e == 0) {   // Ex: half-integer along x
+      s = eps[k * nxy + j * nx + i] + eps[k * nxy + jm * nx + i] + eps[km * nxy + j * nx + i] +
+          eps[km * nxy + jm * nx + i];
+    } else if (e == 1) {   // Ey: half-integer along y
+      s = eps[k * nxy + j * nx + i] + eps[k * nxy + j * nx + im] + eps[km * nxy + j * nx + i] +
+          eps[km * nxy + j * nx + im];
+    } else {               // Ez: half-integer along z
+      s = eps[k * nxy + j * nx + i] + eps[k * nxy + j * nx + im] + eps[k * nxy + jm * nx + i] +
+          eps[k * nxy + jm * nx + im];
+    }
+    return (T)(4.0 / s);
+  }
+  __device__ __forceinline__ T sigma(const Geo& g, const Cell& q, int c) const {
+    const int li = g.la == 0 ? q.i : (g.la == 1 ? q.j : q.k);
+    const int na = g.la == 0 ? g.nx : (g.la == 1 ? g.ny : g.nz);
+    const double pos = li + 0.5 * g.sighalf[c];
+    const double d = fmax(fmax((double)L - pos, pos - (double)(na - L)), 0.0);
+    return (T)(smax * d / (double)L);
+  }
+};
+
+
+// out = A v (TR = 0) or A^T v (TR = 1) at the components of one cell.
+template <typename T, int DIM, int TR, typename Mat>
+__device__ __forceinline__ void stencil(const Geo& g, const T* __restrict__ v, const Mat& mat,
+                                        const Cell& q, T* out) {
+  const int64_t nc = g.ncell;
+  const int i = q.i, j = q.j, k = q.k;
+  if (DIM == 2) {
+    // components 0 Hx (0,1/2), 1 Hy (1/2,0), 2 Ez (0,0)
+    const T Hx = ldv(g, v, 0, q.c0, i, j, k), Hy = ldv(g, v, 1, q.c0, i, j, k);
+    const T Hy_im = ldv(g, v, 1, q.cim, q.im, j, k), Hx_jm = ldv(g, v, 0, q.cjm, i, q.jm, k);
+    T Ez = ldv(g, v, 2, q.c0, i, j, k);
+    T Ez_jp = ldv(g, v, 2, q.cjp, i, q.jp, k), Ez_ip = ldv(g, v, 2, q.cip, q.ip, j, k);
+    const T s0 = mat.sigma(g, q, 0), s1 = mat.sigma(g, q, 1), s2 = mat.sigma(g, q, 2);
+    const T curlH = (Hy - Hy_im) - (Hx - Hx_jm);
+    if (!TR) {
+      out[0] = s0 * Hx + (Ez_jp - Ez);
+      out[1] = s1 * Hy - (Ez_ip - Ez);
+      out[2] = mat.inv_eps(g, 0, q.c0) * (s2 * Ez - curlH);
+    } else {
+      Ez *= mat.inv_eps(g, 0, q.c0);
+      Ez_jp *= mat.inv_eps(g, 0, q.cjp);
+      Ez_ip *= mat.inv_eps(g, 0, q.cip);
+      out[0] = s0 * Hx - (Ez_jp - Ez);
+      out[1] = s1 * Hy + (Ez_ip - Ez);
+      out[2] = s2 * Ez + curlH;
+    }
+  } else {
+    const int ip = q.ip, im = q.im, jp = q.jp, jm = q.jm, kp = q.kp, km = q.km;
+    const T Hx = ldv(g, v, 0, q.c0, i, j, k), Hy = ldv(g, v, 1, q.c0, i, j, k);
+    const T Hz = ldv(g, v, 2, q.c0, i, j, k);
+    T Ex = ldv(g, v, 3, q.c0, i, j, k), Ey = ldv(g, v, 4, q.c0, i, j, k);
+    T Ez = ldv(g, v, 5, q.c0, i, j, k);
+    T Ez_jp = ldv(g, v, 5, q.cjp, i, jp, k), Ey_kp = ldv(g, v, 4, q.ckp, i, j, kp);
+    T Ex_kp = ldv(g, v, 3, q.ckp, i, j, kp), Ez_ip = ldv(g, v, 5, q.cip, ip, j, k);
+    T Ey_ip = ldv(g, v, 4, q.cip, ip, j, k), Ex_jp = ldv(g, v, 3, q.cjp, i, jp, k);
+    const T Hz_jm = ldv(g, v, 2, q.cjm, i, jm, k), Hy_km = ldv(g, v, 1, q.ckm, i, j, km);
+    const T Hx_km = ldv(g, v, 0, q.ckm, i, j, km), Hz_im = ldv(g, v, 2, q.cim, im, j, k);
+    const T Hy_im = ldv(g, v, 1, q.cim, im, j, k), Hx_jm = ldv(g, v, 0, q.cjm, i, jm, k);
+    T s[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s[c] = mat.sigma(g, q, c);
+    const T cHx = (Hz - Hz_jm) - (Hy - Hy_km);
+    const T cHy = (Hx - Hx_km) - (Hz - Hz_im);
+    const T cHz = (Hy - Hy_im) - (Hx - Hx_jm);
+    if (!TR) {
+      out[0] = s[0] * Hx + ((Ez_jp - Ez) - (Ey_kp - Ey));
+      out[1] = s[1] * Hy + ((Ex_kp - Ex) - (Ez_ip - Ez));
+      out[2] = s[2] * Hz + ((Ey_ip - Ey) - (Ex_jp - Ex));
+      out[3] = mat.inv_eps(g, 0, q.c0) * (s[3] * Ex - cHx);
+      out[4] = mat.inv_eps(g, 1, q.c0) * (s[4] * Ey - cHy);
+      out[5] = mat.inv_eps(g, 2, q.c0) * (s[5] * Ez - cHz);
+    } else {
+      Ex *= mat.inv_eps(g, 0, q.c0);
+      Ey *= mat.inv_eps(g, 1, q.c0);
+      Ez *= mat.inv_eps(g, 2, q.c0);
+      Ez_jp *= mat.inv_eps(g, 2, q.cjp);
+      Ey_kp *= mat.inv_eps(g, 1, q.ckp);
+      Ex_kp *= mat.inv_eps(g, 0, q.ckp);
+      Ez_ip *= mat.inv_eps(g, 2, q.cip);
+      Ey_ip *= mat.inv_eps(g, 1, q.cip);
+      Ex_jp *= mat.inv_eps(g, 0, q.cjp);
+      out[0] = s[0] * Hx - ((Ez_jp - Ez) - (Ey_kp - Ey));
+      out[1] = s[1] * Hy - ((Ex_kp - Ex) - (Ez_ip - Ez));
+      out[2] = s[2] * Hz - ((Ey_ip - Ey) - (Ex_jp - Ex));
+      out[3] = s[3] * Ex + cHx;
+      out[4] = s[4] * Ey + cHy;
+      out[5] = s[5] * Ez + cHz;
+    }
+  }
+  constexpr int NC = DIM == 2 ? 3 : 6;
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    if (is_wall(g, c, i, j, k)) out[c] = T(0);
+}
+
+
+}  // namespace kx

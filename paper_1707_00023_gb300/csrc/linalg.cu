@@ -141,7 +141,7 @@ kx_status launch_pass_b(kx_ctx* c, int slot, int j) {
     grid[fp64] = persistent_grid(c, fp64 ? (const void*)k_pass_b<double> : (const void*)k_pass_b<float>,
                                  1 << 30, 0);
   const int64_t rounds = (c->n / (fp64 ? 2 : 4) + NTHREADS - 1) / NTHREADS;
-  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(rounds, grid[fp64]));
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(rounds, grid[fp64]), c->ps));
   if (fp64) {
     k_pass_b<double><<<nb, NTHREADS, 0, c->stream>>>(make_slot<double>(c, slot), j, c->n, c->ld,
                                                     ldh, aug, 1e-12);
@@ -403,7 +403,7 @@ kx_status launch_true_residual(kx_ctx* c, const void* g, int nfreq, const double
                                   cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
-    c->err = std::string("residual read-back failed: ") + cudaGetErrorString(e);
+    snprintf(c->err, sizeof(c->err), "residual read-back failed: %s", cudaGetErrorString(e));
     return KX_ECUDA;
   }
   for (int f = 0; f < nfreq; ++f) out_host[f] = c->h_small[f];

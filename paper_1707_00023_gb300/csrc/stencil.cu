@@ -9,134 +9,9 @@
 // a block close in time and the reuse inside L1/L2.
 #include "kx_internal.cuh"
 #include "kx_reduce.cuh"
+#include "kx_stencil.cuh"
 
 namespace kx {
-
-__device__ __forceinline__ bool is_wall(const Geo& g, int c, int i, int j, int k) {
-  const unsigned mb = g.maskbits[c];
-  return ((mb & 1u) && i == 0) || ((mb & 2u) && j == 0) || ((mb & 4u) && k == 0);
-}
-
-struct Cell {
-  int i, j, k, ip, im, jp, jm, kp, km;
-  int64_t c0, cip, cim, cjp, cjm, ckp, ckm;
-};
-
-__device__ __forceinline__ Cell make_cell(const Geo& g, int64_t cell) {
-  Cell q;
-  q.i = (int)(cell % g.nx);
-  const int64_t r = cell / g.nx;
-  q.j = (int)(r % g.ny);
-  q.k = (int)(r / g.ny);
-  q.ip = (q.i + 1 == g.nx) ? 0 : q.i + 1;
-  q.im = (q.i == 0) ? g.nx - 1 : q.i - 1;
-  q.jp = (q.j + 1 == g.ny) ? 0 : q.j + 1;
-  q.jm = (q.j == 0) ? g.ny - 1 : q.j - 1;
-  q.c0 = cell;
-  q.cip = cell + (q.ip - q.i);
-  q.cim = cell + (q.im - q.i);
-  q.cjp = cell + (int64_t)(q.jp - q.j) * g.nx;
-  q.cjm = cell + (int64_t)(q.jm - q.j) * g.nx;
-  if (g.dim == 3) {
-    const int64_t nxy = (int64_t)g.nx * g.ny;
-    q.kp = (q.k + 1 == g.nz) ? 0 : q.k + 1;
-    q.km = (q.k == 0) ? g.nz - 1 : q.k - 1;
-    q.ckp = cell + (int64_t)(q.kp - q.k) * nxy;
-    q.ckm = cell + (int64_t)(q.km - q.k) * nxy;
-  } else {
-    q.kp = q.km = 0;
-    q.ckp = q.ckm = cell;
-  }
-  return q;
-}
-
-template <typename T>
-__device__ __forceinline__ T ldv(const Geo& g, const T* __restrict__ v, int c, int64_t idx, int i,
-                                 int j, int k) {
-  return is_wall(g, c, i, j, k) ? T(0) : v[(int64_t)c * g.ncell + idx];
-}
-
-template <typename T>
-__device__ __forceinline__ T sig_of(const Geo& g, const T* __restrict__ sig2, const Cell& q, int c) {
-  const int li = g.la == 0 ? q.i : (g.la == 1 ? q.j : q.k);
-  return sig2[2 * li + g.sighalf[c]];
-}
-
-// out = A v (TR = 0) or A^T v (TR = 1) at the components of one cell.
-template <typename T, int DIM, int TR>
-__device__ __forceinline__ void stencil(const Geo& g, const T* __restrict__ v,
-                                        const T* __restrict__ ie, const T* __restrict__ sig2,
-                                        const Cell& q, T* out) {
-  const int64_t nc = g.ncell;
-  const int i = q.i, j = q.j, k = q.k;
-  if (DIM == 2) {
-    // components 0 Hx (0,1/2), 1 Hy (1/2,0), 2 Ez (0,0)
-    const T Hx = ldv(g, v, 0, q.c0, i, j, k), Hy = ldv(g, v, 1, q.c0, i, j, k);
-    const T Hy_im = ldv(g, v, 1, q.cim, q.im, j, k), Hx_jm = ldv(g, v, 0, q.cjm, i, q.jm, k);
-    T Ez = ldv(g, v, 2, q.c0, i, j, k);
-    T Ez_jp = ldv(g, v, 2, q.cjp, i, q.jp, k), Ez_ip = ldv(g, v, 2, q.cip, q.ip, j, k);
-    const T s0 = sig_of(g, sig2, q, 0), s1 = sig_of(g, sig2, q, 1), s2 = sig_of(g, sig2, q, 2);
-    const T curlH = (Hy - Hy_im) - (Hx - Hx_jm);
-    if (!TR) {
-      out[0] = s0 * Hx + (Ez_jp - Ez);
-      out[1] = s1 * Hy - (Ez_ip - Ez);
-      out[2] = ie[q.c0] * (s2 * Ez - curlH);
-    } else {
-      Ez *= ie[q.c0];
-      Ez_jp *= ie[q.cjp];
-      Ez_ip *= ie[q.cip];
-      out[0] = s0 * Hx - (Ez_jp - Ez);
-      out[1] = s1 * Hy + (Ez_ip - Ez);
-      out[2] = s2 * Ez + curlH;
-    }
-  } else {
-    const int ip = q.ip, im = q.im, jp = q.jp, jm = q.jm, kp = q.kp, km = q.km;
-    const T Hx = ldv(g, v, 0, q.c0, i, j, k), Hy = ldv(g, v, 1, q.c0, i, j, k);
-    const T Hz = ldv(g, v, 2, q.c0, i, j, k);
-    T Ex = ldv(g, v, 3, q.c0, i, j, k), Ey = ldv(g, v, 4, q.c0, i, j, k);
-    T Ez = ldv(g, v, 5, q.c0, i, j, k);
-    T Ez_jp = ldv(g, v, 5, q.cjp, i, jp, k), Ey_kp = ldv(g, v, 4, q.ckp, i, j, kp);
-    T Ex_kp = ldv(g, v, 3, q.ckp, i, j, kp), Ez_ip = ldv(g, v, 5, q.cip, ip, j, k);
-    T Ey_ip = ldv(g, v, 4, q.cip, ip, j, k), Ex_jp = ldv(g, v, 3, q.cjp, i, jp, k);
-    const T Hz_jm = ldv(g, v, 2, q.cjm, i, jm, k), Hy_km = ldv(g, v, 1, q.ckm, i, j, km);
-    const T Hx_km = ldv(g, v, 0, q.ckm, i, j, km), Hz_im = ldv(g, v, 2, q.cim, im, j, k);
-    const T Hy_im = ldv(g, v, 1, q.cim, im, j, k), Hx_jm = ldv(g, v, 0, q.cjm, i, jm, k);
-    T s[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) s[c] = sig_of(g, sig2, q, c);
-    const T cHx = (Hz - Hz_jm) - (Hy - Hy_km);
-    const T cHy = (Hx - Hx_km) - (Hz - Hz_im);
-    const T cHz = (Hy - Hy_im) - (Hx - Hx_jm);
-    if (!TR) {
-      out[0] = s[0] * Hx + ((Ez_jp - Ez) - (Ey_kp - Ey));
-      out[1] = s[1] * Hy + ((Ex_kp - Ex) - (Ez_ip - Ez));
-      out[2] = s[2] * Hz + ((Ey_ip - Ey) - (Ex_jp - Ex));
-      out[3] = ie[q.c0] * (s[3] * Ex - cHx);
-      out[4] = ie[nc + q.c0] * (s[4] * Ey - cHy);
-      out[5] = ie[2 * nc + q.c0] * (s[5] * Ez - cHz);
-    } else {
-      Ex *= ie[q.c0];
-      Ey *= ie[nc + q.c0];
-      Ez *= ie[2 * nc + q.c0];
-      Ez_jp *= ie[2 * nc + q.cjp];
-      Ey_kp *= ie[nc + q.ckp];
-      Ex_kp *= ie[q.ckp];
-      Ez_ip *= ie[2 * nc + q.cip];
-      Ey_ip *= ie[nc + q.cip];
-      Ex_jp *= ie[q.cjp];
-      out[0] = s[0] * Hx - ((Ez_jp - Ez) - (Ey_kp - Ey));
-      out[1] = s[1] * Hy - ((Ex_kp - Ex) - (Ez_ip - Ez));
-      out[2] = s[2] * Hz - ((Ey_ip - Ey) - (Ex_jp - Ex));
-      out[3] = s[3] * Ex + cHx;
-      out[4] = s[4] * Ey + cHy;
-      out[5] = s[5] * Ez + cHz;
-    }
-  }
-  constexpr int NC = DIM == 2 ? 3 : 6;
-#pragma unroll
-  for (int c = 0; c < NC; ++c)
-    if (is_wall(g, c, i, j, k)) out[c] = T(0);
-}
 
 // ---------------------------------------------------------------------------
 // Material set-up: 1/eps on E nodes (mean over the cells whose closure holds
@@ -211,7 +86,7 @@ __global__ void __launch_bounds__(NTHREADS) k_apply(Geo g, const T* __restrict__
        cell += (int64_t)gridDim.x * blockDim.x) {
     const Cell q = make_cell(g, cell);
     T o[NC];
-    stencil<T, DIM, TR>(g, v, ie, sig2, q, o);
+    stencil<T, DIM, TR>(g, v, TableMat<T>{ie, sig2}, q, o);
 #pragma unroll
     for (int c = 0; c < NC; ++c) w[(int64_t)c * g.ncell + cell] = o[c];
   }
@@ -249,10 +124,8 @@ kx_status launch_apply(kx_ctx* c, const void* v, void* w, int transpose) {
 //   w = A v_j  (v_j = scale[j] * V_j)       [augmented: w = [A y - (a/eta) g; -W b; W a]]
 //   d_i = V_i^T w for i <= j, and ||w||^2, fused in one sweep over the cells.
 // The last block forms H[i, j] = scale[i] * d_i.
-template <typename T, int DIM, int AUG>
-__global__ void __launch_bounds__(NTHREADS) k_pass_a(Geo g, Slot<T> s, int j, int64_t ld, int ldh,
-                                                    const T* __restrict__ ie,
-                                                    const T* __restrict__ sig2,
+template <typename T, int DIM, int AUG, typename Mat>
+__global__ void __launch_bounds__(NTHREADS) k_pass_a(Geo g, Slot<T> s, int j, int64_t ld, Mat mat,
                                                     const T* __restrict__ gsrc) {
   constexpr int NC = DIM == 2 ? 3 : 6;
   if (s.st->done) return;
@@ -275,7 +148,7 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_a(Geo g, Slot<T> s, int j, in
     T o[NC];
     if (act) {
       const Cell q = make_cell(g, cell);
-      stencil<T, DIM, 0>(g, vin, ie, sig2, q, o);
+      stencil<T, DIM, 0>(g, vin, mat, q, o);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         o[c] *= tsj;
@@ -552,11 +425,11 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int j, const void* gaug) {
   if (!gr) {
     const void* fn;
     if (vec4) fn = gaug ? (const void*)k_pass_a4<1> : (const void*)k_pass_a4<0>;
-    else if (g.dim == 2) fn = gaug ? (const void*)k_pass_a<T, 2, 1> : (const void*)k_pass_a<T, 2, 0>;
-    else fn = gaug ? (const void*)k_pass_a<T, 3, 1> : (const void*)k_pass_a<T, 3, 0>;
+    else if (g.dim == 2) fn = gaug ? (const void*)k_pass_a<T, 2, 1, TableMat<T>> : (const void*)k_pass_a<T, 2, 0, TableMat<T>>;
+    else fn = gaug ? (const void*)k_pass_a<T, 3, 1, TableMat<T>> : (const void*)k_pass_a<T, 3, 0, TableMat<T>>;
     gr = persistent_grid(c, fn, 1 << 30, 0);
   }
-  const int nb = (int)std::min<int64_t>(rounds, gr);
+  const int nb = (int)std::min<int64_t>(std::min<int64_t>(rounds, gr), c->ps);
   if (vec4) {
     Slot<float> sf = make_slot<float>(c, slot);
     const float* ief = (const float*)c->d_inv_eps;
@@ -564,11 +437,11 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int j, const void* gaug) {
     if (gaug) k_pass_a4<1><<<nb, NTHREADS, 0, c->stream>>>(g, sf, j, c->ld, ief, sgf, (const float*)gaug);
     else k_pass_a4<0><<<nb, NTHREADS, 0, c->stream>>>(g, sf, j, c->ld, ief, sgf, nullptr);
   } else if (g.dim == 2) {
-    if (gaug) k_pass_a<T, 2, 1><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, ldh, ie, sg, gs);
-    else k_pass_a<T, 2, 0><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, ldh, ie, sg, gs);
+    if (gaug) k_pass_a<T, 2, 1, TableMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
+    else k_pass_a<T, 2, 0, TableMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
   } else {
-    if (gaug) k_pass_a<T, 3, 1><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, ldh, ie, sg, gs);
-    else k_pass_a<T, 3, 0><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, ldh, ie, sg, gs);
+    if (gaug) k_pass_a<T, 3, 1, TableMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
+    else k_pass_a<T, 3, 0, TableMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
   }
   KX_CHECK_LAUNCH(c);
   const int dbl = sizeof(T) == 8;
@@ -576,6 +449,34 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int j, const void* gaug) {
                                              ldh, nb, gaug != nullptr);
   KX_CHECK_LAUNCH(c);
   return KX_OK;
+}
+
+// Pass A with the permittivity read per cell (CellMat): the variant used
+// by the allocation-free entry point, which holds no 1/eps table.
+template <typename T>
+static kx_status pass_a_cells_t(kx_ctx* c, int slot, int j, const double* eps) {
+  const Geo& g = c->geo;
+  Slot<T> s = make_slot<T>(c, slot);
+  const CellMat<T> mat{eps, c->d.sigma_max, c->d.layer_cells};
+  const int64_t rounds = (g.ncell + NTHREADS - 1) / NTHREADS;
+  static int grid[2] = {0, 0};
+  int& gr = grid[g.dim == 3];
+  if (!gr)
+    gr = persistent_grid(c, g.dim == 2 ? (const void*)k_pass_a<T, 2, 0, CellMat<T>>
+                                       : (const void*)k_pass_a<T, 3, 0, CellMat<T>>, 1 << 30, 0);
+  const int nb = (int)std::min<int64_t>(std::min<int64_t>(rounds, gr), c->ps);
+  if (g.dim == 2) k_pass_a<T, 2, 0, CellMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr);
+  else k_pass_a<T, 3, 0, CellMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr);
+  KX_CHECK_LAUNCH(c);
+  k_fin_a<<<j + 2, NTHREADS, 0, c->stream>>>(make_slot<float>(c, slot), make_slot<double>(c, slot),
+                                             sizeof(T) == 8, j, c->m + 1, nb, 0);
+  KX_CHECK_LAUNCH(c);
+  return KX_OK;
+}
+
+kx_status launch_pass_a_cells(kx_ctx* c, int slot, int j, const double* d_eps_cell) {
+  return c->d.precision == KX_FP64 ? pass_a_cells_t<double>(c, slot, j, d_eps_cell)
+                                   : pass_a_cells_t<float>(c, slot, j, d_eps_cell);
 }
 
 // Algorithmic bytes of pass A at step j: read v_j and V_0..V_{j-1} (j+1
