@@ -35,6 +35,9 @@ WORKLOADS = {
                           prec="fp32", method="split", rtol=1e-7, t_oracle=20.0),
     "3d64_m64_T400_plain": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=1,
                                 prec="fp32", method="plain", rtol=1e-7, t_oracle=20.0),
+    # the same medium at 8 frequencies in [0.8, 1.2] Omega0, advanced in one lockstep batch
+    "3d64_m64_T400_8f_plain": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=8,
+                                   prec="fp32", method="plain", rtol=1e-7, t_oracle=20.0, batch=8),
     # 2D 64^2, 40 disks, FP64, m = 30, T = 200, plain method
     "2d64_m30_T200": dict(dim=2, n=64, seed=1708, T=200.0, m=30, nfreq=1, prec="fp64",
                           method="plain", rtol=1e-11, t_oracle=200.0),
@@ -199,7 +202,7 @@ def main():
     dt = torch.float64 if w["prec"] == "fp64" else torch.float32
     stream = torch.cuda.Stream()
     ctx = Context(sc.grid, sc.eps_cell, precision=w["prec"], krylov_dim=w["m"],
-                  max_freqs=w["nfreq"], stream=stream)
+                  max_freqs=w["nfreq"], batch=w.get("batch", 1), stream=stream)
     g_host = torch.tensor(sc.g, dtype=dt).pin_memory()
     g = g_host.to("cuda")
     torch.cuda.synchronize()

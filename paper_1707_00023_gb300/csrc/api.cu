@@ -81,39 +81,54 @@ SlotState fresh_state() {
   return s;
 }
 
-// m Arnoldi steps on slot `slot` from its (already normalised) column 0.
-kx_status arnoldi_steps(kx_ctx* c, int slot, int m, const void* g_aug) {
+// m Arnoldi steps on slots [slot0, slot0 + ns) from their (normalised)
+// column 0, all slots in the same launches.
+kx_status arnoldi_steps(kx_ctx* c, int slot0, int ns, int m, const void* g_aug) {
   for (int j = 0; j < m; ++j) {
-    KX_TRY(launch_pass_a(c, slot, j, g_aug));
-    KX_TRY(launch_pass_b(c, slot, j));
+    KX_TRY(launch_pass_a(c, slot0, ns, j, g_aug));
+    KX_TRY(launch_pass_b(c, slot0, ns, j));
   }
-  c->stats.arnoldi_steps += m;
-  c->stats.matvecs += m;
+  c->stats.arnoldi_steps += (int64_t)m * ns;
+  c->stats.matvecs += (int64_t)m * ns;
   return KX_OK;
 }
 
-// Exponential Krylov restarted in time (Sect. 3.3): the state in column 0 of
-// `slot` is advanced to st.T by sub-steps x <- V_m exp(-t H_m) beta e_1.
-kx_status time_loop(kx_ctx* c, int slot, const void* g_aug, double* err_est) {
-  KX_TRY(launch_norm_init(c, slot));
+kx_status read_states(kx_ctx* c, int slot0, int ns) {
+  KX_CUDA(c, cudaMemcpyAsync(c->h_state + slot0, c->d_state + slot0, sizeof(SlotState) * ns,
+                             cudaMemcpyDeviceToHost, c->stream), "state read");
+  return sync(c);
+}
+
+// Exponential Krylov restarted in time (Sect. 3.3): the states in column 0
+// of slots [slot0, slot0 + ns) advance together to their final times by
+// sub-steps x <- V_m exp(-t H_m) beta e_1; a slot that has arrived retires and
+// every later kernel skips it.
+kx_status time_loop(kx_ctx* c, int slot0, int ns, const void* g_aug, double* err_est) {
+  KX_TRY(launch_norm_init(c, slot0, ns));
   const int max_sub = 20000;
-  SlotState st;
-  for (int it = 0; it < max_sub; ++it) {
-    KX_TRY(arnoldi_steps(c, slot, c->m, g_aug));
-    KX_TRY(launch_substep_control(c, slot));
-    KX_TRY(launch_combine(c, slot));
-    KX_TRY(read_state(c, slot, &st));
-    if (st.status) {
-      return fail(c, (kx_status)st.status,
-                  st.status == KX_ENOCONV ? "time sub-step control: no step length met the tolerance"
-                                          : "non-finite value in the Krylov process");
+  bool all = false;
+  for (int it = 0; it < max_sub && !all; ++it) {
+    KX_TRY(arnoldi_steps(c, slot0, ns, c->m, g_aug));
+    KX_TRY(launch_substep_control(c, slot0, ns));
+    KX_TRY(launch_combine(c, slot0, ns));
+    KX_TRY(read_states(c, slot0, ns));
+    all = true;
+    for (int q = 0; q < ns; ++q) {
+      const SlotState& st = c->h_state[slot0 + q];
+      if (st.status)
+        return fail(c, (kx_status)st.status,
+                    st.status == KX_ENOCONV ? "time sub-step control: no step length met the tolerance"
+                                            : "non-finite value in the Krylov process");
+      all = all && st.retired;
     }
-    if (st.finished) break;
   }
-  if (!st.finished) return fail(c, KX_ENOCONV, "time stepping: sub-step cap reached");
-  c->stats.substeps += st.substeps;
-  c->stats.expm_evals += st.expm_evals;
-  if (err_est) *err_est = st.err_acc;
+  if (!all) return fail(c, KX_ENOCONV, "time stepping: sub-step cap reached");
+  for (int q = 0; q < ns; ++q) {
+    const SlotState& st = c->h_state[slot0 + q];
+    c->stats.substeps += st.substeps;
+    c->stats.expm_evals += st.expm_evals;
+    if (err_est) err_est[q] = st.err_acc;
+  }
   return KX_OK;
 }
 
@@ -138,7 +153,7 @@ kx_status stationary_core(kx_ctx* c, const void* d_g, const double* omegas, int 
   KX_CUDA(c, cudaMemcpyAsync(slot_col(c, slot, 0), d_g, c->n * c->esize, cudaMemcpyDeviceToDevice,
                              c->stream), "copy g");
   KX_TRY(upload_state(c, slot, fresh_state()));
-  KX_TRY(launch_norm_init(c, slot));
+  KX_TRY(launch_norm_init(c, slot, 1));
   SlotState st;
   KX_TRY(read_state(c, slot, &st));
   const double beta = st.beta;
@@ -162,7 +177,7 @@ kx_status stationary_core(kx_ctx* c, const void* d_g, const double* omegas, int 
   double best = INFINITY;
   int since_best = 0;
   for (int cyc = 0; matvecs < max_matvecs; ++cyc) {
-    KX_TRY(arnoldi_steps(c, slot, c->m, nullptr));
+    KX_TRY(arnoldi_steps(c, slot, 1, c->m, nullptr));
     KX_TRY(read_state(c, slot, &st));
     if (st.status) return fail(c, (kx_status)st.status, "non-finite value in the Arnoldi process");
     const int md = st.m_done;
@@ -183,7 +198,7 @@ kx_status stationary_core(kx_ctx* c, const void* d_g, const double* omegas, int 
     // restart from v_{m+1}: copy column md to column 0 and renormalise
     KX_CUDA(c, cudaMemcpyAsync(slot_col(c, slot, 0), slot_col(c, slot, md), c->n * c->esize,
                                cudaMemcpyDeviceToDevice, c->stream), "restart copy");
-    KX_TRY(launch_norm_init(c, slot));
+    KX_TRY(launch_norm_init(c, slot, 1));
   }
   if (matvecs_out) *matvecs_out = matvecs;
   if (rel_resid) KX_TRY(launch_true_residual(c, d_g, nfreq, omegas, zre, zim, rel_resid));
@@ -364,11 +379,11 @@ kx_status arnoldi(kx_ctx* c, const void* d_v0, int m, void* d_V, double* H, doub
                              c->stream), "copy v0");
   KX_CUDA(c, cudaMemsetAsync(c->d_H, 0, (size_t)(c->m + 1) * c->m * sizeof(double), c->stream), "zero H");
   KX_TRY(upload_state(c, slot, fresh_state()));
-  KX_TRY(launch_norm_init(c, slot));
+  KX_TRY(launch_norm_init(c, slot, 1));
   SlotState st;
   KX_TRY(read_state(c, slot, &st));
   if (!(st.beta > 0.0) || !std::isfinite(st.beta)) return fail(c, KX_ENONFINITE, "v0 is zero or non-finite");
-  KX_TRY(arnoldi_steps(c, slot, m, nullptr));
+  KX_TRY(arnoldi_steps(c, slot, 1, m, nullptr));
   KX_TRY(read_state(c, slot, &st));
   if (st.status) return fail(c, (kx_status)st.status, "non-finite value in the Arnoldi process");
   *beta = st.beta;
@@ -448,7 +463,7 @@ kx_status expm_action(kx_ctx* c, const void* d_y0, double T, double rtol, void* 
   s.rtol = rtol;
   s.tol_mode = 0;
   KX_TRY(upload_state(c, slot, s));
-  KX_TRY(time_loop(c, slot, nullptr, err_est));
+  KX_TRY(time_loop(c, slot, 1, nullptr, err_est));
   KX_CUDA(c, cudaMemcpyAsync(d_y, slot_col(c, slot, 0), c->n * c->esize, cudaMemcpyDeviceToDevice,
                              c->stream), "copy y");
   return sync(c);
@@ -486,39 +501,47 @@ kx_status response_at_freqs(kx_ctx* c, const void* d_g, const double* omegas, in
     KX_CUDA(c, cudaMemcpyAsync(slot_col(c, slot, 0), d_g, c->n * c->esize, cudaMemcpyDeviceToDevice,
                                c->stream), "copy g");
     KX_TRY(upload_state(c, slot, fresh_state()));
-    KX_TRY(launch_norm_init(c, slot));
+    KX_TRY(launch_norm_init(c, slot, 1));
   }
   SlotState gst;
   KX_TRY(read_state(c, slot, &gst));
   const double gnorm = gst.beta;
-  for (int f = 0; f < nfreq; ++f) {
-    SlotState s = fresh_state();
-    s.T = T;
-    s.rtol = rtol;
-    double ef = 0.0;
-    if (method == KX_SPLIT) {
-      // transient y^(T) = exp(-TA) Im z_f  (eq. (y_homo))
-      KX_CUDA(c, cudaMemcpyAsync(slot_col(c, slot, 0), vec_ptr(c, c->d_zim, f), c->n * c->esize,
-                                 cudaMemcpyDeviceToDevice, c->stream), "copy Im z");
-      s.tol_mode = 0;
-      KX_TRY(upload_state(c, slot, s));
-      KX_TRY(time_loop(c, slot, nullptr, &ef));
-    } else {
-      // augmented system x' = -[[A, -g/eta, 0], [0, 0, -W], [0, W, 0]] x,
-      // x(0) = [0; 0; eta]: the two extra entries are eta (sin Wt, cos Wt)
-      KX_CUDA(c, cudaMemsetAsync(slot_col(c, slot, 0), 0, c->n * c->esize, c->stream), "zero y");
-      s.aug = 1;
-      s.omega = omegas[f];
-      s.eta = gnorm > 0.0 ? gnorm : 1.0;
-      s.tol_mode = 1;
-      KX_TRY(upload_state(c, slot, s));
-      KX_TRY(time_loop(c, slot, d_g, &ef));
+  // frequencies advance in waves of up to `batch` slots sharing every launch
+  const int B = c->d.batch;
+  for (int f0 = 0; f0 < nfreq; f0 += B) {
+    const int ns = std::min(B, nfreq - f0);
+    for (int q = 0; q < ns; ++q) {
+      const int f = f0 + q;
+      SlotState s = fresh_state();
+      s.T = T;
+      s.rtol = rtol;
+      if (method == KX_SPLIT) {
+        // transient y^(T) = exp(-TA) Im z_f  (eq. (y_homo))
+        KX_CUDA(c, cudaMemcpyAsync(slot_col(c, q, 0), vec_ptr(c, c->d_zim, f), c->n * c->esize,
+                                   cudaMemcpyDeviceToDevice, c->stream), "copy Im z");
+        s.tol_mode = 0;
+      } else {
+        // augmented system x' = -[[A, -g/eta, 0], [0, 0, -W], [0, W, 0]] x,
+        // x(0) = [0; 0; eta]: the two extra entries are eta (sin Wt, cos Wt)
+        KX_CUDA(c, cudaMemsetAsync(slot_col(c, q, 0), 0, c->n * c->esize, c->stream), "zero y");
+        s.aug = 1;
+        s.omega = omegas[f];
+        s.eta = gnorm > 0.0 ? gnorm : 1.0;
+        s.tol_mode = 1;
+      }
+      c->h_state[q] = s;
     }
-    if (err_est) err_est[f] = ef;
-    void* Ep = d_E_plane ? (char*)d_E_plane + (int64_t)f * nE * np * c->esize : nullptr;
-    void* Yf = d_Y ? vec_ptr(c, d_Y, f) : nullptr;
-    KX_TRY(launch_response(c, f, omegas, T, method == KX_SPLIT, vec_ptr(c, c->d_zre, f),
-                           vec_ptr(c, c->d_zim, f), slot_col(c, slot, 0), axis, idx, Ep, d_int + f, Yf));
+    KX_CUDA(c, cudaMemcpyAsync(c->d_state, c->h_state, sizeof(SlotState) * ns, cudaMemcpyHostToDevice,
+                               c->stream), "state upload");
+    KX_TRY(sync(c));
+    KX_TRY(time_loop(c, 0, ns, method == KX_SPLIT ? nullptr : d_g, err_est ? err_est + f0 : nullptr));
+    for (int q = 0; q < ns; ++q) {
+      const int f = f0 + q;
+      void* Ep = d_E_plane ? (char*)d_E_plane + (int64_t)f * nE * np * c->esize : nullptr;
+      void* Yf = d_Y ? vec_ptr(c, d_Y, f) : nullptr;
+      KX_TRY(launch_response(c, f, omegas, T, method == KX_SPLIT, vec_ptr(c, c->d_zre, f),
+                             vec_ptr(c, c->d_zim, f), slot_col(c, q, 0), axis, idx, Ep, d_int + f, Yf));
+    }
   }
   if (intensity) {
     KX_CUDA(c, cudaMemcpyAsync(c->h_small, d_int, sizeof(double) * nfreq, cudaMemcpyDeviceToHost, c->stream),

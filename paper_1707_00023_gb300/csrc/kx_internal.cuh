@@ -48,6 +48,7 @@ struct SlotState {
   int k_acc;
   int substeps;
   int expm_evals;
+  int retired;       // final combination done: every later kernel skips this slot
 };
 
 // Pointers of one slot's workspace.
@@ -63,6 +64,27 @@ struct Slot {
   double* u;         // projected coefficients (m)
   SlotState* st;
 };
+
+// Consecutive slots: slot y's pointers are slot 0's plus y times the strides.
+template <typename T>
+struct SlotSet {
+  Slot<T> s0;
+  int64_t sV, saug, sH, sscale, spart, su;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ Slot<T> slot_at(const SlotSet<T>& ss, int y) {
+  Slot<T> s = ss.s0;
+  s.V += y * ss.sV;
+  s.aug += y * ss.saug;
+  s.H += y * ss.sH;
+  s.scale += y * ss.sscale;
+  s.part += y * ss.spart;
+  s.u += y * ss.su;
+  s.counter += 8 * y;
+  s.st += y;
+  return s;
+}
 
 struct Material {
   const void* inv_eps;   // (ncomp - nh) x ncell, 1 / mean eps on E nodes
@@ -120,17 +142,17 @@ struct kx_ctx {
 // Launch helpers implemented in the .cu files.
 namespace kx {
 
-// stencil.cu
+// stencil.cu  (slot0, ns: the consecutive slots [slot0, slot0 + ns) advance together)
 kx_status launch_setup_material(kx_ctx* c);
 kx_status launch_apply(kx_ctx* c, const void* v, void* w, int transpose);
-kx_status launch_pass_a(kx_ctx* c, int slot, int j, const void* g_aug);
+kx_status launch_pass_a(kx_ctx* c, int slot0, int ns, int j, const void* g_aug);
 // pass A reading the per-cell permittivity directly (no 1/eps table)
 kx_status launch_pass_a_cells(kx_ctx* c, int slot, int j, const double* d_eps_cell);
-kx_status launch_pass_b(kx_ctx* c, int slot, int j);
+kx_status launch_pass_b(kx_ctx* c, int slot0, int ns, int j);
 
 // linalg.cu
-kx_status launch_norm_init(kx_ctx* c, int slot);
-kx_status launch_combine(kx_ctx* c, int slot);
+kx_status launch_norm_init(kx_ctx* c, int slot0, int ns);
+kx_status launch_combine(kx_ctx* c, int slot0, int ns);
 kx_status launch_basis_export(kx_ctx* c, int slot, void* dV, int m);
 kx_status launch_zupdate(kx_ctx* c, int slot, int nfreq, void* zre, void* zim, int m);
 kx_status launch_true_residual(kx_ctx* c, const void* g, int nfreq, const double* d_om,
@@ -140,7 +162,7 @@ kx_status launch_response(kx_ctx* c, int f, const double* h_om, double T, int sp
                           int plane_idx, void* E_plane, double* d_intensity, void* Yout);
 
 // projected.cu
-kx_status launch_substep_control(kx_ctx* c, int slot);
+kx_status launch_substep_control(kx_ctx* c, int slot0, int ns);
 kx_status launch_expm_project(kx_ctx* c, const double* dH, int ldh, int m, double beta,
                               double tau, const double* d_om, int nfreq, double* d_u);
 kx_status launch_shifted_solve(kx_ctx* c, int slot, int nfreq, int m);
@@ -173,6 +195,20 @@ inline Slot<T> make_slot(kx_ctx* c, int slot) {
   s.u = c->d_u + (int64_t)slot * (m + 2);
   s.st = c->d_state + slot;
   return s;
+}
+
+template <typename T>
+inline SlotSet<T> make_slotset(kx_ctx* c, int slot0) {
+  SlotSet<T> ss;
+  const int m = c->m;
+  ss.s0 = make_slot<T>(c, slot0);
+  ss.sV = (int64_t)(m + 1) * c->ld;
+  ss.saug = (int64_t)(m + 1) * 2;
+  ss.sH = (int64_t)(m + 1) * m;
+  ss.sscale = m + 2;
+  ss.spart = (int64_t)PCOLS * c->ps;
+  ss.su = m + 2;
+  return ss;
 }
 }  // namespace kx
 

@@ -40,11 +40,12 @@ template <> __device__ __forceinline__ double2 vzero<double>() { return make_dou
 // column stays unnormalised (delayed normalisation); a lucky breakdown
 // h_{j+1,j} <= tol * max_i ||A v_i|| stops the process.
 template <typename T>
-__global__ void __launch_bounds__(NTHREADS) k_pass_b(Slot<T> s, int j, int64_t n, int64_t ld,
+__global__ void __launch_bounds__(NTHREADS) k_pass_b(SlotSet<T> ss, int j, int64_t n, int64_t ld,
                                                     int ldh, int aug, double btol) {
   using V4 = typename Vec<T>::t;
   constexpr int W = Vec<T>::w;
-  if (s.st->done) return;
+  const Slot<T> s = slot_at(ss, blockIdx.y);
+  if (s.st->done || s.st->retired) return;
   __shared__ T coef[MMAX + 1];
   const int ncol = j + 1;
   for (int q = threadIdx.x; q < ncol; q += blockDim.x)
@@ -89,8 +90,9 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_b(Slot<T> s, int j, int64_t n
 
 // Finalisation of pass B (one block): h_{j+1,j} = ||w||, scale, breakdown.
 template <typename T>
-__global__ void __launch_bounds__(NTHREADS) k_fin_b(Slot<T> s, int j, int ldh, int nb, int aug, double btol) {
-  if (s.st->done) return;
+__global__ void __launch_bounds__(NTHREADS) k_fin_b(SlotSet<T> ss, int j, int ldh, int nb, int aug, double btol) {
+  const Slot<T> s = slot_at(ss, blockIdx.y);
+  if (s.st->done || s.st->retired) return;
   const int ncol = j + 1;
   double x = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) x += __ldcg(s.part + b);
@@ -130,11 +132,11 @@ __global__ void __launch_bounds__(NTHREADS) k_fin_b(Slot<T> s, int j, int ldh, i
 
 // Algorithmic bytes of pass B at step j: read w and V_0..V_j (j+2 vectors),
 // write the updated column (1).
-kx_status launch_pass_b(kx_ctx* c, int slot, int j) {
+kx_status launch_pass_b(kx_ctx* c, int slot, int ns, int j) {
   const int ldh = c->m + 1;
   const int aug = 1;  // augmented entries are zero when unused
   time_begin(c);
-  struct End { kx_ctx* c; int j; ~End() { time_end(c, KX_K_PASS_B, (j + 3.0) * c->n * c->esize); } } end{c, j};
+  struct End { kx_ctx* c; int j, ns; ~End() { time_end(c, KX_K_PASS_B, (j + 3.0) * c->n * c->esize * ns); } } end{c, j, ns};
   static int grid[2] = {0, 0};
   const int fp64 = c->d.precision == KX_FP64;
   if (!grid[fp64])
@@ -143,15 +145,15 @@ kx_status launch_pass_b(kx_ctx* c, int slot, int j) {
   const int64_t rounds = (c->n / (fp64 ? 2 : 4) + NTHREADS - 1) / NTHREADS;
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(rounds, grid[fp64]), c->ps));
   if (fp64) {
-    k_pass_b<double><<<nb, NTHREADS, 0, c->stream>>>(make_slot<double>(c, slot), j, c->n, c->ld,
-                                                    ldh, aug, 1e-12);
+    k_pass_b<double><<<dim3(nb, ns), NTHREADS, 0, c->stream>>>(make_slotset<double>(c, slot), j, c->n, c->ld,
+                                                              ldh, aug, 1e-12);
     KX_CHECK_LAUNCH(c);
-    k_fin_b<double><<<1, NTHREADS, 0, c->stream>>>(make_slot<double>(c, slot), j, ldh, nb, aug, 1e-12);
+    k_fin_b<double><<<dim3(1, ns), NTHREADS, 0, c->stream>>>(make_slotset<double>(c, slot), j, ldh, nb, aug, 1e-12);
   } else {
-    k_pass_b<float><<<nb, NTHREADS, 0, c->stream>>>(make_slot<float>(c, slot), j, c->n, c->ld,
-                                                   ldh, aug, 1e-6);
+    k_pass_b<float><<<dim3(nb, ns), NTHREADS, 0, c->stream>>>(make_slotset<float>(c, slot), j, c->n, c->ld,
+                                                             ldh, aug, 1e-6);
     KX_CHECK_LAUNCH(c);
-    k_fin_b<float><<<1, NTHREADS, 0, c->stream>>>(make_slot<float>(c, slot), j, ldh, nb, aug, 1e-6);
+    k_fin_b<float><<<dim3(1, ns), NTHREADS, 0, c->stream>>>(make_slotset<float>(c, slot), j, ldh, nb, aug, 1e-6);
   }
   KX_CHECK_LAUNCH(c);
   return KX_OK;
@@ -164,9 +166,11 @@ kx_status launch_pass_b(kx_ctx* c, int slot, int j) {
 // (upd1)); in the augmented case the phase entries are then reset to their
 // exact values eta (sin W t, cos W t).
 template <typename T>
-__global__ void __launch_bounds__(NTHREADS) k_restart(Slot<T> s, int64_t n, int64_t ld, int mode) {
+__global__ void __launch_bounds__(NTHREADS) k_restart(SlotSet<T> ss, int64_t n, int64_t ld, int mode) {
   using V4 = typename Vec<T>::t;
   constexpr int W = Vec<T>::w;
+  const Slot<T> s = slot_at(ss, blockIdx.y);
+  if (s.st->retired) return;
   __shared__ T coef[MMAX];
   int m = 0;
   if (mode == 1) {
@@ -245,25 +249,26 @@ __global__ void __launch_bounds__(NTHREADS) k_restart(Slot<T> s, int64_t n, int6
     if (!isfinite(b)) s.st->status = KX_ENONFINITE;
     s.st->m_done = 0;
     s.st->wmax = 0.0;
+    if (mode == 1 && s.st->finished) s.st->retired = 1;
   }
 }
 
 template <typename T>
-static kx_status restart_t(kx_ctx* c, int slot, int mode) {
+static kx_status restart_t(kx_ctx* c, int slot, int ns, int mode) {
   // bytes: combine reads the m basis columns and writes one; norm reads one
   time_begin(c);
-  k_restart<T><<<c->nblk, NTHREADS, 0, c->stream>>>(make_slot<T>(c, slot), c->n, c->ld, mode);
-  time_end(c, KX_K_RESTART, (mode == 1 ? c->m + 1.0 : 1.0) * c->n * c->esize);
+  k_restart<T><<<dim3(c->nblk, ns), NTHREADS, 0, c->stream>>>(make_slotset<T>(c, slot), c->n, c->ld, mode);
+  time_end(c, KX_K_RESTART, (mode == 1 ? c->m + 1.0 : 1.0) * c->n * c->esize * ns);
   KX_CHECK_LAUNCH(c);
   return KX_OK;
 }
 
-kx_status launch_norm_init(kx_ctx* c, int slot) {
-  return c->d.precision == KX_FP64 ? restart_t<double>(c, slot, 0) : restart_t<float>(c, slot, 0);
+kx_status launch_norm_init(kx_ctx* c, int slot, int ns) {
+  return c->d.precision == KX_FP64 ? restart_t<double>(c, slot, ns, 0) : restart_t<float>(c, slot, ns, 0);
 }
 
-kx_status launch_combine(kx_ctx* c, int slot) {
-  return c->d.precision == KX_FP64 ? restart_t<double>(c, slot, 1) : restart_t<float>(c, slot, 1);
+kx_status launch_combine(kx_ctx* c, int slot, int ns) {
+  return c->d.precision == KX_FP64 ? restart_t<double>(c, slot, ns, 1) : restart_t<float>(c, slot, ns, 1);
 }
 
 // ---------------------------------------------------------------------------

@@ -213,7 +213,11 @@ size_t expm_smem_bytes(int msz) { return (size_t)6 * msz * msz * sizeof(double);
 // whose integrated residual (trapezoid rule, an error bound for a
 // contractive exp(-tA)) stays below tol_rate * t_k is accepted; if none,
 // tau shrinks 4x and the table is rebuilt.
-__global__ void __launch_bounds__(256) k_substep(double* H, int ldh, double* u_out, SlotState* st, int K) {
+__global__ void __launch_bounds__(256) k_substep(SlotSet<float> ss, int ldh, int K) {
+  const Slot<float> sl = slot_at(ss, blockIdx.x);
+  const double* H = sl.H;
+  double* u_out = sl.u;
+  SlotState* st = sl.st;
   extern __shared__ double sm[];
   __shared__ double red[32];
   __shared__ double lv[72];
@@ -221,13 +225,13 @@ __global__ void __launch_bounds__(256) k_substep(double* H, int ldh, double* u_o
   __shared__ int piv;
   __shared__ double s_err, s_tau;
   __shared__ int s_kacc, s_retry;
-  if (st->finished || st->status) return;
+  if (st->finished || st->status || st->retired) return;
   const int m = st->m_done;
   if (m <= 0 || st->beta == 0.0) {
     if (threadIdx.x == 0) {
       st->t_now = st->T;
       st->finished = 1;
-      for (int i = 0; i < MMAX; ++i) u_out[i] = 0.0;
+      for (int i = 0; i < ldh - 1; ++i) u_out[i] = 0.0;
     }
     return;
   }
@@ -321,7 +325,7 @@ __global__ void __launch_bounds__(256) k_substep(double* H, int ldh, double* u_o
   }
 }
 
-kx_status launch_substep_control(kx_ctx* c, int slot) {
+kx_status launch_substep_control(kx_ctx* c, int slot, int ns) {
   const int m = c->m;
   const size_t sm = expm_smem_bytes(m);
   static int attr_done = 0;
@@ -329,9 +333,8 @@ kx_status launch_substep_control(kx_ctx* c, int slot) {
     cudaFuncSetAttribute(k_substep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)expm_smem_bytes(MMAX + 2));
     attr_done = 1;
   }
-  Slot<double> s = make_slot<double>(c, slot);
   time_begin(c);
-  k_substep<<<1, 256, sm, c->stream>>>(s.H, m + 1, s.u, s.st, 32);
+  k_substep<<<ns, 256, sm, c->stream>>>(make_slotset<float>(c, slot), m + 1, 32);
   time_end(c, KX_K_PROJ, 0.0);
   KX_CHECK_LAUNCH(c);
   return KX_OK;

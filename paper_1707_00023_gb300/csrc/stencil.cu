@@ -125,10 +125,11 @@ kx_status launch_apply(kx_ctx* c, const void* v, void* w, int transpose) {
 //   d_i = V_i^T w for i <= j, and ||w||^2, fused in one sweep over the cells.
 // The last block forms H[i, j] = scale[i] * d_i.
 template <typename T, int DIM, int AUG, typename Mat>
-__global__ void __launch_bounds__(NTHREADS) k_pass_a(Geo g, Slot<T> s, int j, int64_t ld, Mat mat,
+__global__ void __launch_bounds__(NTHREADS) k_pass_a(Geo g, SlotSet<T> ss, int j, int64_t ld, Mat mat,
                                                     const T* __restrict__ gsrc) {
   constexpr int NC = DIM == 2 ? 3 : 6;
-  if (s.st->done) return;
+  const Slot<T> s = slot_at(ss, blockIdx.y);
+  if (s.st->done || s.st->retired) return;
   __shared__ double acc[NWARPS][MMAX + 2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int q = threadIdx.x; q < NWARPS * (MMAX + 2); q += blockDim.x) (&acc[0][0])[q] = 0.0;
@@ -222,11 +223,12 @@ __device__ __forceinline__ float wall1(const Geo& g, int c, float v, int i, int 
 }
 
 template <int AUG>
-__global__ void __launch_bounds__(NTHREADS) k_pass_a4(Geo g, Slot<float> s, int j, int64_t ld,
+__global__ void __launch_bounds__(NTHREADS) k_pass_a4(Geo g, SlotSet<float> ss, int j, int64_t ld,
                                                      const float* __restrict__ ie,
                                                      const float* __restrict__ sig2,
                                                      const float* __restrict__ gsrc) {
-  if (s.st->done) return;
+  const Slot<float> s = slot_at(ss, blockIdx.y);
+  if (s.st->done || s.st->retired) return;
   __shared__ double acc[NWARPS][MMAX + 2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int q = threadIdx.x; q < NWARPS * (MMAX + 2); q += blockDim.x) (&acc[0][0])[q] = 0.0;
@@ -360,15 +362,15 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_a4(Geo g, Slot<float> s, int 
 // partials of column c in a fixed order; columns c <= j give
 // H[c, j] = scale[c] * d_c (plus the augmented entries' share), column j+1
 // gives ||w|| (breakdown scale) and the augmented entries of w.
-__global__ void __launch_bounds__(NTHREADS) k_fin_a(Slot<float> sf, Slot<double> sd, int dbl, int j, int ldh,
-                                                   int nb, int aug) {
-  double* part = dbl ? sd.part : sf.part;
-  const int ps = dbl ? sd.ps : sf.ps;
-  double* H = dbl ? sd.H : sf.H;
-  double* scale = dbl ? sd.scale : sf.scale;
-  double* augv = dbl ? sd.aug : sf.aug;
-  SlotState* st = dbl ? sd.st : sf.st;
-  if (st->done) return;
+__global__ void __launch_bounds__(NTHREADS) k_fin_a(SlotSet<float> ss, int j, int ldh, int nb, int aug) {
+  const Slot<float> sl = slot_at(ss, blockIdx.y);
+  double* part = sl.part;
+  const int ps = sl.ps;
+  double* H = sl.H;
+  double* scale = sl.scale;
+  double* augv = sl.aug;
+  SlotState* st = sl.st;
+  if (st->done || st->retired) return;
   const int col = blockIdx.x;
   const int ncol = j + 1;
   double x = 0.0;
@@ -406,10 +408,10 @@ __global__ void __launch_bounds__(NTHREADS) k_fin_a(Slot<float> sf, Slot<double>
 }
 
 template <typename T>
-static kx_status pass_a_t(kx_ctx* c, int slot, int j, const void* gaug) {
+static kx_status pass_a_t(kx_ctx* c, int slot, int ns, int j, const void* gaug) {
   const Geo& g = c->geo;
   const int m = c->m;
-  Slot<T> s = make_slot<T>(c, slot);
+  SlotSet<T> s = make_slotset<T>(c, slot);
   const T* ie = (const T*)c->d_inv_eps;
   const T* sg = (const T*)c->d_sig2;
   const T* gs = (const T*)gaug;
@@ -430,23 +432,23 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int j, const void* gaug) {
     gr = persistent_grid(c, fn, 1 << 30, 0);
   }
   const int nb = (int)std::min<int64_t>(std::min<int64_t>(rounds, gr), c->ps);
+  const dim3 grd(nb, ns);
   if (vec4) {
-    Slot<float> sf = make_slot<float>(c, slot);
+    SlotSet<float> sf = make_slotset<float>(c, slot);
     const float* ief = (const float*)c->d_inv_eps;
     const float* sgf = (const float*)c->d_sig2;
-    if (gaug) k_pass_a4<1><<<nb, NTHREADS, 0, c->stream>>>(g, sf, j, c->ld, ief, sgf, (const float*)gaug);
-    else k_pass_a4<0><<<nb, NTHREADS, 0, c->stream>>>(g, sf, j, c->ld, ief, sgf, nullptr);
+    if (gaug) k_pass_a4<1><<<grd, NTHREADS, 0, c->stream>>>(g, sf, j, c->ld, ief, sgf, (const float*)gaug);
+    else k_pass_a4<0><<<grd, NTHREADS, 0, c->stream>>>(g, sf, j, c->ld, ief, sgf, nullptr);
   } else if (g.dim == 2) {
-    if (gaug) k_pass_a<T, 2, 1, TableMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
-    else k_pass_a<T, 2, 0, TableMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
+    if (gaug) k_pass_a<T, 2, 1, TableMat<T>><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
+    else k_pass_a<T, 2, 0, TableMat<T>><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
   } else {
-    if (gaug) k_pass_a<T, 3, 1, TableMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
-    else k_pass_a<T, 3, 0, TableMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
+    if (gaug) k_pass_a<T, 3, 1, TableMat<T>><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
+    else k_pass_a<T, 3, 0, TableMat<T>><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
   }
   KX_CHECK_LAUNCH(c);
-  const int dbl = sizeof(T) == 8;
-  k_fin_a<<<j + 2, NTHREADS, 0, c->stream>>>(make_slot<float>(c, slot), make_slot<double>(c, slot), dbl, j,
-                                             ldh, nb, gaug != nullptr);
+  k_fin_a<<<dim3(j + 2, ns), NTHREADS, 0, c->stream>>>(make_slotset<float>(c, slot), j, ldh, nb,
+                                                       gaug != nullptr);
   KX_CHECK_LAUNCH(c);
   return KX_OK;
 }
@@ -456,7 +458,7 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int j, const void* gaug) {
 template <typename T>
 static kx_status pass_a_cells_t(kx_ctx* c, int slot, int j, const double* eps) {
   const Geo& g = c->geo;
-  Slot<T> s = make_slot<T>(c, slot);
+  SlotSet<T> s = make_slotset<T>(c, slot);
   const CellMat<T> mat{eps, c->d.sigma_max, c->d.layer_cells};
   const int64_t rounds = (g.ncell + NTHREADS - 1) / NTHREADS;
   static int grid[2] = {0, 0};
@@ -468,8 +470,7 @@ static kx_status pass_a_cells_t(kx_ctx* c, int slot, int j, const double* eps) {
   if (g.dim == 2) k_pass_a<T, 2, 0, CellMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr);
   else k_pass_a<T, 3, 0, CellMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr);
   KX_CHECK_LAUNCH(c);
-  k_fin_a<<<j + 2, NTHREADS, 0, c->stream>>>(make_slot<float>(c, slot), make_slot<double>(c, slot),
-                                             sizeof(T) == 8, j, c->m + 1, nb, 0);
+  k_fin_a<<<j + 2, NTHREADS, 0, c->stream>>>(make_slotset<float>(c, slot), j, c->m + 1, nb, 0);
   KX_CHECK_LAUNCH(c);
   return KX_OK;
 }
@@ -481,14 +482,14 @@ kx_status launch_pass_a_cells(kx_ctx* c, int slot, int j, const double* d_eps_ce
 
 // Algorithmic bytes of pass A at step j: read v_j and V_0..V_{j-1} (j+1
 // vectors), write w (1), read 1/eps on the E nodes, and g when augmented.
-kx_status launch_pass_a(kx_ctx* c, int slot, int j, const void* g_aug) {
+kx_status launch_pass_a(kx_ctx* c, int slot, int ns, int j, const void* g_aug) {
   const double vb = (double)c->n * c->esize;
   const double bytes = (j + 2) * vb + (double)(c->geo.ncomp - c->geo.nh) * c->geo.ncell * c->esize +
                        (g_aug ? vb : 0.0);
   time_begin(c);
-  const kx_status st = c->d.precision == KX_FP64 ? pass_a_t<double>(c, slot, j, g_aug)
-                                                 : pass_a_t<float>(c, slot, j, g_aug);
-  time_end(c, KX_K_PASS_A, bytes);
+  const kx_status st = c->d.precision == KX_FP64 ? pass_a_t<double>(c, slot, ns, j, g_aug)
+                                                 : pass_a_t<float>(c, slot, ns, j, g_aug);
+  time_end(c, KX_K_PASS_A, bytes * ns);
   return st;
 }
 

@@ -261,3 +261,41 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(KxError):
         Context(sc.grid, eps, precision="fp64")
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batched_frequencies_match_one_at_a_time(prec):
+    """Frequencies advanced in lockstep waves (batch 2, 5 frequencies: waves of
+    2, 2, 1) give the same responses as one frequency at a time, and match the
+    oracle."""
+    sc = S.config_3d(n=12, fill=0.3, T=20.0)
+    A = yee.Operator(sc.grid, sc.eps_cell).matrix()
+    oms = S.freq_list(5)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    g = dev(sc.g, dt)
+    rtol = 1e-11 if prec == "fp64" else 1e-7
+    outs = []
+    for batch in (1, 2):
+        ctx = Context(sc.grid, sc.eps_cell, precision=prec, krylov_dim=24, max_freqs=5, batch=batch)
+        outs.append(ctx.response_at_freqs(g, oms, sc.T, rtol=rtol, method="plain", plane=sc.plane,
+                                          want_full=True))
+        ctx.close()
+    y1 = outs[0]["Y"].double().cpu().numpy()
+    y2 = outs[1]["Y"].double().cpu().numpy()
+    assert np.array_equal(y1, y2)                       # same kernels, same reduction order
+    np.testing.assert_array_equal(outs[0]["intensity"], outs[1]["intensity"])
+    tol = 1e-10 if prec == "fp64" else 1e-6
+    for f, om in enumerate(oms):
+        assert rel(y2[f], exact.y_plain(A, sc.g, om, sc.T)) < tol
+
+
+def test_batched_split_transients():
+    sc = S.config_2d(n=12, ndisks=2, T=30.0)
+    A = yee.Operator(sc.grid, sc.eps_cell).matrix()
+    oms = S.freq_list(3)
+    ctx = Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=40, max_freqs=3, batch=3)
+    out = ctx.response_at_freqs(dev(sc.g, torch.float64), oms, sc.T, rtol=1e-11, method="split",
+                                plane=sc.plane, want_full=True)
+    for f, om in enumerate(oms):
+        assert rel(out["Y"][f].cpu().numpy(), exact.y_plain(A, sc.g, om, sc.T)) < 1e-10
+    ctx.close()
