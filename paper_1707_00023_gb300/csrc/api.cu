@@ -322,6 +322,7 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_state, 0, (size_t)B * sizeof(SlotState), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_V, 0, bytes_V, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_aug, 0, (size_t)B * (m + 1) * 2 * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_H, 0, (size_t)B * (m + 1) * m * sizeof(double), c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->d_eps_cell, eps_cell, (size_t)ncell * sizeof(double), cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) {

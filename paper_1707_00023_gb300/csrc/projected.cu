@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(256) k_substep(SlotSet<float> ss, int ldh, int
     const double dt = tau / K;
     for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
       const int r = idx / m, c = idx - r * m;
-      buf[0][idx] = -dt * H[r + (int64_t)c * ldh];
+      // upper Hessenberg: the Arnoldi process writes nothing below the subdiagonal
+      buf[0][idx] = (r <= c + 1) ? -dt * H[r + (int64_t)c * ldh] : 0.0;
     }
     __syncthreads();
     double* X = cta_expm(buf, m, red, lv, &piv);

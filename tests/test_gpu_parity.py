@@ -299,3 +299,35 @@ def test_batched_split_transients():
     for f, om in enumerate(oms):
         assert rel(out["Y"][f].cpu().numpy(), exact.y_plain(A, sc.g, om, sc.T)) < 1e-10
     ctx.close()
+
+
+def test_full_size_3d64_against_oracle_short_T():
+    """Full 3D 64^3 grid and Krylov dimension 64 of the benchmark, T = 20:
+    every field value of the FP32 response against the FP64 oracle."""
+    sc = S.config_3d(n=64, seed=1709, fill=0.3, T=20.0, m=64)
+    A = yee.Operator(sc.grid, sc.eps_cell).matrix()
+    ctx = Context(sc.grid, sc.eps_cell, precision="fp32", krylov_dim=64, max_freqs=2, batch=2)
+    oms = S.freq_list(2)
+    out = ctx.response_at_freqs(dev(sc.g, torch.float32), oms, sc.T, rtol=1e-7, method="plain",
+                                plane=sc.plane, want_full=True)
+    want = exact.y_plain(A, sc.g, oms[0], sc.T)
+    assert rel(out["Y"][0].double().cpu().numpy(), want) < 1e-6
+    ctx.close()
+
+
+def test_full_size_3d64_T400_fp32_vs_fp64():
+    """The benchmark's configuration (3D 64^3, m = 64, T = 400): the FP32
+    batch against the FP64 path (itself oracle-checked to 1e-10) on the first
+    and last of 32 frequencies; the accuracy target is 1e-6 relative L2."""
+    sc = S.config_3d(n=64, seed=1709, fill=0.3, T=400.0, m=64)
+    oms = S.freq_list(32)[[0, 31]]
+    g32 = dev(sc.g, torch.float32)
+    ctx = Context(sc.grid, sc.eps_cell, precision="fp32", krylov_dim=64, max_freqs=2, batch=2)
+    a = ctx.response_at_freqs(g32, oms, sc.T, rtol=1e-7, method="plain", plane=sc.plane, want_full=True)
+    ctx.close()
+    ctx = Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=64, max_freqs=2, batch=2)
+    b = ctx.response_at_freqs(dev(sc.g, torch.float64), oms, sc.T, rtol=1e-11, method="plain",
+                              plane=sc.plane, want_full=True)
+    ctx.close()
+    for f in range(2):
+        assert rel(a["Y"][f].double().cpu().numpy(), b["Y"][f].cpu().numpy()) < 1e-6
