@@ -28,6 +28,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "freq responses/s at 1e-6 rel err vs per-freq Krylov; A·v+GS HBM GB/s"
 
+# DRAM bytes / algorithmic bytes per launch of the two hot kernels, from the
+# ncu capture summarised in profiles/arnoldi_passes_3d64_ncu.md (8-frequency
+# batch, step j = 50).  Set to None whenever those kernels change.
+NCU_TRAFFIC_RATIO = {"k_pass_a": 1.0015, "k_pass_b": 1.000}
+
 WORKLOADS = {
     # 3D Yee 64^3, random eps=2.25 spheres (fill 0.3, r 2-5), 8-cell layer,
     # Ex plane source, FP32 vectors / FP64 projected, m = 64, T = 400
@@ -274,8 +279,13 @@ def main():
     ab_bytes = kt["pass_a"]["bytes"] + kt["pass_b"]["bytes"]
     ab_ms = kt["pass_a"]["ms"] + kt["pass_b"]["ms"]
     ab_gbs = ab_bytes / (ab_ms / 1000.0) / 1e9 if ab_ms > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": f"k_pass_{dom[-1]}", "achieved": round(ach, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
+    kname = f"k_pass_{dom[-1]}"
+    avg_bytes = kt[dom]["bytes"] / max(1, kt[dom]["launches"])
+    ratio = NCU_TRAFFIC_RATIO.get(kname)
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(ach, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                "traffic": None if ratio is None else round(ratio * avg_bytes),
+                "algorithmic_bytes_per_launch": round(avg_bytes),
                 "peak_source": peak_kind,
                 "launches": kt[dom]["launches"], "avg_launch_us": round(1000 * kt[dom]["ms"] / max(1, kt[dom]["launches"]), 2),
                 "share_of_step": round(kt[dom]["ms"] / total_ms, 4) if total_ms else None}
