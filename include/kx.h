@@ -70,6 +70,8 @@ typedef struct {
   int krylov_dim;     /* m, 2 <= m <= 64: Arnoldi steps per restart          */
   int max_freqs;      /* largest nfreq of any later call, 1 .. 64            */
   int batch;          /* bases held for concurrent transients, >= 1          */
+  int max_checkpoints; /* forward states kept for the adjoint (0: no adjoint;
+                          otherwise batch >= 2); one per time sub-step       */
 } kx_desc;
 
 typedef struct kx_ctx kx_ctx;
@@ -176,6 +178,30 @@ kx_status response_at_freqs(kx_ctx* ctx, const void* d_g, const double* omegas,
                             int nfreq, double T, double rtol, int method,
                             const int* plane, void* d_E_plane, double* intensity,
                             double* err_est, void* d_Y);
+
+/* Gradient of the summed output-plane intensity
+ *     L = sum_j sum_plane |E_j(T)|^2,   E_j from response_at_freqs(KX_PLAIN),
+ * with respect to the per-cell permittivity (the paper has no gradient; this
+ * is the adjoint of eq. (ode)):
+ *     dL/deps_c = -sum_j int_0^T lambda_j(t)^T (dA/deps_c) y_j(t) dt,
+ *     lambda_j(t) = exp(-(T - t) A^T) 2 P^T P y_j(T).
+ * The forward solution is stored at every time sub-step (at most
+ * max_checkpoints of them); backwards, each sub-step's forward Krylov basis
+ * is recomputed from its checkpoint and lambda is carried by exponential
+ * Krylov on A^T; the time integral is composite Gauss-Legendre quadrature on
+ * the exact projected solutions.
+ *   d_grad_eps: device, ncell doubles (x fastest), receives dL/deps.
+ *   loss: host, receives L.
+ * Requires a context created with max_checkpoints > 0 (and batch >= 2).
+ * Synchronises the stream.  KX_ENOMEM if the sub-steps exceed the
+ * checkpoints. */
+kx_status adjoint_response_grad(kx_ctx* ctx, const void* d_g, const double* omegas, int nfreq,
+                                double T, double rtol, const int* plane, double* d_grad_eps,
+                                double* loss);
+
+/* Replace the per-cell permittivity of a context (host or device array of
+ * ncell doubles, each > 0); the grid and workspace stay.  Synchronises. */
+kx_status kx_set_permittivity(kx_ctx* ctx, const double* eps_cell);
 
 /* Counters; kx_reset_stats zeroes them. */
 kx_status kx_get_stats(const kx_ctx* ctx, kx_stats* out);

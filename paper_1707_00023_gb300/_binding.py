@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "KX_OK", 1: "KX_EINVAL", 2: "KX_ENOMEM", 3: "KX_ECUDA",
 EXPORTS = ["krylov_expm_create", "krylov_expm_destroy", "kx_num_unknowns", "apply_A",
            "arnoldi", "expm_phi_project", "stationary_solve", "expm_action",
            "response_at_freqs", "kx_get_stats", "kx_reset_stats", "kx_set_timing",
-           "kx_kernel_times", "kx_last_error", "kx_arnoldi_noalloc", "kx_noalloc_last_error"]
+           "kx_kernel_times", "kx_last_error", "kx_arnoldi_noalloc", "kx_noalloc_last_error",
+           "adjoint_response_grad", "kx_set_permittivity"]
 KCLASSES = ["pass_a", "pass_b", "restart", "projected", "zupdate", "apply"]
 
 
@@ -39,7 +40,8 @@ class Desc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("bc", ctypes.c_int * 3),
                 ("layer_axis", ctypes.c_int), ("layer_cells", ctypes.c_int),
                 ("sigma_max", ctypes.c_double), ("precision", ctypes.c_int),
-                ("krylov_dim", ctypes.c_int), ("max_freqs", ctypes.c_int), ("batch", ctypes.c_int)]
+                ("krylov_dim", ctypes.c_int), ("max_freqs", ctypes.c_int), ("batch", ctypes.c_int),
+                ("max_checkpoints", ctypes.c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -80,6 +82,9 @@ def load_library(path: Optional[str] = None):
                                       ctypes.c_int, ip, vp, dp, dp, vp]
     lib.kx_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.kx_reset_stats.argtypes = [vp]
+    lib.adjoint_response_grad.argtypes = [vp, vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ip, vp, dp]
+    lib.kx_set_permittivity.argtypes = [vp, vp]
     lib.kx_set_timing.argtypes = [vp, ctypes.c_int]
     lib.kx_kernel_times.argtypes = [vp, ctypes.POINTER(KernelTime)]
     lib.kx_last_error.argtypes = [vp]
@@ -109,7 +114,7 @@ class Context:
     """
 
     def __init__(self, grid, eps_cell, precision: str = "fp32", krylov_dim: int = 64,
-                 max_freqs: int = 1, batch: int = 1, stream=None):
+                 max_freqs: int = 1, batch: int = 1, stream=None, max_checkpoints: int = 0):
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -127,6 +132,7 @@ class Context:
         d.krylov_dim = krylov_dim
         d.max_freqs = max_freqs
         d.batch = batch
+        d.max_checkpoints = max_checkpoints
         self.desc = d
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -263,3 +269,49 @@ class Context:
         if not (allow_noconv and st == KX_ENOCONV):
             self._check(st)
         return {"E_plane": Ep, "intensity": inten, "err_est": err, "Y": Y, "status": st}
+
+    def set_permittivity(self, eps_cell):
+        """Replace the per-cell permittivity (numpy array or CUDA float64 tensor)."""
+        torch = self._torch
+        if isinstance(eps_cell, torch.Tensor) and eps_cell.is_cuda:
+            e = eps_cell.detach().to(torch.float64).contiguous()
+            self._check(self.lib.kx_set_permittivity(self.h, ctypes.c_void_p(e.data_ptr())))
+        else:
+            e = np.ascontiguousarray(np.asarray(eps_cell, np.float64).reshape(-1))
+            self._check(self.lib.kx_set_permittivity(self.h, e.ctypes.data_as(ctypes.c_void_p)))
+
+    def adjoint_response_grad(self, g, omegas, T, rtol=1e-8, plane=(0, 0)):
+        """(L, dL/deps) for L = summed output-plane intensity over the frequencies.
+
+        dL/deps is a CUDA float64 tensor with the grid's cell shape."""
+        om = np.ascontiguousarray(np.asarray(omegas, np.float64))
+        grad = self._torch.empty(int(np.prod(self.grid.n)), dtype=self._torch.float64, device="cuda")
+        loss = ctypes.c_double()
+        pl = (ctypes.c_int * 2)(int(plane[0]), int(plane[1]))
+        self._check(self.lib.adjoint_response_grad(self.h, self._vec(g, "g"), _dptr(om), len(om), float(T),
+                                                   float(rtol), pl, ctypes.c_void_p(grad.data_ptr()),
+                                                   ctypes.byref(loss)))
+        return loss.value, grad.reshape(tuple(reversed(self.grid.n)))
+
+
+def intensity_loss(ctx, eps_cell, g, omegas, T, rtol=1e-8, plane=(0, 0)):
+    """Differentiable summed output-plane intensity L(eps) (torch scalar).
+
+    Forward and gradient both come from ``adjoint_response_grad``; the
+    context's permittivity is replaced by ``eps_cell`` first."""
+    import torch
+
+    class _IntensityLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, eps):
+            ctx.set_permittivity(eps)
+            loss, grad = ctx.adjoint_response_grad(g, omegas, T, rtol, plane)
+            fctx.save_for_backward(grad)
+            return torch.tensor(loss, dtype=torch.float64, device=eps.device)
+
+        @staticmethod
+        def backward(fctx, gout):
+            (grad,) = fctx.saved_tensors
+            return gout * grad.to(gout.device)
+
+    return _IntensityLoss.apply(eps_cell)

@@ -230,6 +230,8 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
   if (d.krylov_dim < 2 || d.krylov_dim > MMAX) return fail(nullptr, KX_EINVAL, "krylov_dim must be 2..64");
   if (d.max_freqs < 1 || d.max_freqs > MAXF) return fail(nullptr, KX_EINVAL, "max_freqs must be 1..64");
   if (d.batch < 1 || d.batch > 64) return fail(nullptr, KX_EINVAL, "batch must be 1..64");
+  if (d.max_checkpoints < 0 || (d.max_checkpoints > 0 && d.batch < 2))
+    return fail(nullptr, KX_EINVAL, "max_checkpoints must be >= 0, and the adjoint needs batch >= 2");
   const int nz = d.dim == 3 ? d.n[2] : 1;
   const int64_t ncell = (int64_t)d.n[0] * d.n[1] * nz;
   for (int64_t i = 0; i < ncell; ++i)
@@ -311,6 +313,35 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
       return fail(nullptr, KX_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
     }
   }
+  if (d.max_checkpoints > 0) {
+    const int P = gauss_points();
+    c->adj_nq_max = 64 * P;
+    const int64_t nE = (int64_t)(g.ncomp - g.nh) * ncell;
+    Alloc adj[] = {
+        {(void**)&c->d_ckpt, (size_t)d.max_checkpoints * c->ld * c->esize},
+        {(void**)&c->d_adj_Q, (size_t)nE * sizeof(double)},
+        {(void**)&c->d_adj_alpha, (size_t)c->adj_nq_max * (MMAX + 1) * sizeof(float)},
+        {(void**)&c->d_adj_omg, (size_t)c->adj_nq_max * MMAX * sizeof(float)},
+        {(void**)&c->d_adj_cw, (size_t)c->adj_nq_max * sizeof(float)},
+        {(void**)&c->d_adj_sn, (size_t)c->adj_nq_max * sizeof(float)},
+        {(void**)&c->d_gauss, (size_t)2 * P * sizeof(double)},
+    };
+    for (auto& a : adj) {
+      e = cudaMalloc(a.p, a.bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        krylov_expm_destroy(c);
+        return fail(nullptr, KX_ENOMEM, std::string("adjoint allocation failed: ") + cudaGetErrorString(e));
+      }
+    }
+    std::vector<double> gw(2 * P);
+    gauss_legendre01(P, gw.data(), gw.data() + P);
+    e = cudaMemcpy(c->d_gauss, gw.data(), sizeof(double) * 2 * P, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      krylov_expm_destroy(c);
+      return fail(nullptr, KX_ECUDA, std::string("Gauss nodes upload failed: ") + cudaGetErrorString(e));
+    }
+  }
   e = cudaMallocHost((void**)&c->h_state, (size_t)B * sizeof(SlotState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_small, 256 * sizeof(double));
   if (e != cudaSuccess) {
@@ -349,7 +380,9 @@ kx_status krylov_expm_destroy(kx_ctx* c) {
   cudaStreamSynchronize(c->stream);
   void* ptrs[] = {c->d_inv_eps, c->d_sig2, c->d_eps_cell, c->d_V, c->d_aug, c->d_H, c->d_scale,
                   c->d_part, c->d_counter, c->d_u, c->d_state, c->d_rho, c->d_coef, c->d_coefd,
-                  c->d_omegas, c->d_small, c->d_tmp, c->d_tmp2, c->d_expm_ws, c->d_zre, c->d_zim};
+                  c->d_omegas, c->d_small, c->d_tmp, c->d_tmp2, c->d_expm_ws, c->d_zre, c->d_zim,
+                  c->d_ckpt, c->d_adj_Q, c->d_adj_alpha, c->d_adj_omg, c->d_adj_cw, c->d_adj_sn,
+                  c->d_gauss};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_state) cudaFreeHost(c->h_state);
@@ -552,6 +585,131 @@ kx_status response_at_freqs(kx_ctx* c, const void* d_g, const double* omegas, in
   }
   KX_TRY(sync(c));
   if (conv != KX_OK) return fail(c, conv, "stationary solve did not reach its tolerance");
+  return KX_OK;
+}
+
+kx_status kx_set_permittivity(kx_ctx* c, const double* eps_cell) {
+  if (!c || !eps_cell) return KX_EINVAL;
+  const size_t bytes = (size_t)c->geo.ncell * sizeof(double);
+  if (is_device_ptr(eps_cell)) {
+    KX_CUDA(c, cudaMemcpyAsync(c->d_eps_cell, eps_cell, bytes, cudaMemcpyDeviceToDevice, c->stream), "eps copy");
+  } else {
+    for (int64_t i = 0; i < c->geo.ncell; ++i)
+      if (!(eps_cell[i] > 0.0) || !std::isfinite(eps_cell[i]))
+        return fail(c, KX_ENONFINITE, "eps_cell must be finite and > 0");
+    KX_CUDA(c, cudaMemcpyAsync(c->d_eps_cell, eps_cell, bytes, cudaMemcpyHostToDevice, c->stream), "eps copy");
+  }
+  KX_TRY(launch_setup_material(c));
+  return sync(c);
+}
+
+kx_status adjoint_response_grad(kx_ctx* c, const void* d_g, const double* omegas, int nfreq, double T,
+                                double rtol, const int* plane, double* d_grad, double* loss) {
+  if (!c) return KX_EINVAL;
+  KX_TRY(check_vec(c, d_g, "d_g"));
+  KX_TRY(check_omegas(c, omegas, nfreq));
+  if (!d_grad || !loss || !plane) return fail(c, KX_EINVAL, "NULL argument");
+  if (c->d.max_checkpoints <= 0) return fail(c, KX_EINVAL, "context created without checkpoint storage");
+  if (!(T > 0.0) || !std::isfinite(T) || !(rtol > 0.0)) return fail(c, KX_EINVAL, "bad T or rtol");
+  const int axis = plane[0], idx = plane[1];
+  if (axis < 0 || axis >= c->d.dim) return fail(c, KX_EINVAL, "bad plane axis");
+  const int na = axis == 0 ? c->geo.nx : (axis == 1 ? c->geo.ny : c->geo.nz);
+  if (idx < 0 || idx >= na) return fail(c, KX_EINVAL, "bad plane index");
+  const int64_t nE = (int64_t)(c->geo.ncomp - c->geo.nh) * c->geo.ncell;
+  KX_CUDA(c, cudaMemsetAsync(c->d_adj_Q, 0, (size_t)nE * sizeof(double), c->stream), "zero Q");
+  // ||g|| balances the augmented phase entries (as in response_at_freqs)
+  KX_CUDA(c, cudaMemcpyAsync(slot_col(c, 0, 0), d_g, c->n * c->esize, cudaMemcpyDeviceToDevice, c->stream),
+          "copy g");
+  KX_TRY(upload_state(c, 0, fresh_state()));
+  KX_TRY(launch_norm_init(c, 0, 1));
+  SlotState gst;
+  KX_TRY(read_state(c, 0, &gst));
+  const double eta = gst.beta > 0.0 ? gst.beta : 1.0;
+  double* d_int = c->d_small + 128;
+  const size_t vbytes = (size_t)c->n * c->esize;
+  for (int f = 0; f < nfreq; ++f) {
+    const double W = omegas[f];
+    // forward solution with a checkpoint at the start of every sub-step
+    KX_CUDA(c, cudaMemsetAsync(slot_col(c, 0, 0), 0, vbytes, c->stream), "zero y");
+    SlotState s = fresh_state();
+    s.T = T;
+    s.rtol = rtol;
+    s.aug = 1;
+    s.omega = W;
+    s.eta = eta;
+    s.tol_mode = 1;
+    KX_TRY(upload_state(c, 0, s));
+    KX_TRY(launch_norm_init(c, 0, 1));
+    std::vector<double> tk, tauk;
+    double tnow = 0.0;
+    for (;;) {
+      if ((int)tk.size() >= c->d.max_checkpoints)
+        return fail(c, KX_ENOMEM, "adjoint: more time sub-steps than max_checkpoints");
+      KX_CUDA(c, cudaMemcpyAsync((char*)c->d_ckpt + tk.size() * c->ld * c->esize, slot_col(c, 0, 0), vbytes,
+                                 cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
+      tk.push_back(tnow);
+      KX_TRY(arnoldi_steps(c, 0, 1, c->m, d_g));
+      KX_TRY(launch_substep_control(c, 0, 1));
+      KX_TRY(launch_combine(c, 0, 1));
+      KX_TRY(read_states(c, 0, 1));
+      const SlotState& st = c->h_state[0];
+      if (st.status) return fail(c, (kx_status)st.status, "adjoint forward: Krylov process failed");
+      tauk.push_back(st.t_acc);
+      tnow = st.t_now;
+      if (st.retired) break;
+    }
+    c->stats.substeps += (int64_t)tk.size();
+    // loss and lambda(T) = 2 P^T P y(T) in slot 1
+    KX_TRY(launch_response(c, f, omegas, T, 0, nullptr, nullptr, slot_col(c, 0, 0), axis, idx, nullptr,
+                           d_int + f, nullptr));
+    KX_CUDA(c, cudaMemsetAsync(slot_col(c, 1, 0), 0, vbytes, c->stream), "zero lambda");
+    KX_TRY(launch_adj_seed(c, slot_col(c, 0, 0), slot_col(c, 1, 0), axis, idx));
+    // backwards over the sub-steps
+    for (int k = (int)tk.size() - 1; k >= 0; --k) {
+      KX_CUDA(c, cudaMemcpyAsync(slot_col(c, 0, 0), (char*)c->d_ckpt + (size_t)k * c->ld * c->esize, vbytes,
+                                 cudaMemcpyDeviceToDevice, c->stream), "restore checkpoint");
+      SlotState s0 = fresh_state();
+      s0.T = T;
+      s0.aug = 1;
+      s0.omega = W;
+      s0.eta = eta;
+      s0.t_now = tk[k];
+      c->h_state[0] = s0;
+      c->h_state[1] = fresh_state();
+      KX_CUDA(c, cudaMemcpyAsync(c->d_state, c->h_state, 2 * sizeof(SlotState), cudaMemcpyHostToDevice,
+                                 c->stream), "state upload");
+      KX_TRY(sync(c));
+      KX_TRY(launch_norm_init(c, 0, 2));
+      for (int j = 0; j < c->m; ++j) {
+        KX_TRY(launch_pass_a(c, 0, 1, j, d_g));
+        KX_TRY(launch_pass_b(c, 0, 1, j));
+      }
+      for (int j = 0; j < c->m; ++j) {
+        KX_TRY(launch_pass_a_tr(c, 1, 1, j));
+        KX_TRY(launch_pass_b(c, 1, 1, j));
+      }
+      c->stats.arnoldi_steps += 2 * (int64_t)c->m;
+      c->stats.matvecs += 2 * (int64_t)c->m;
+      KX_TRY(read_states(c, 0, 2));
+      if (c->h_state[0].status || c->h_state[1].status)
+        return fail(c, KX_ENONFINITE, "adjoint backward: Krylov process failed");
+      KX_CUDA(c, cudaMemsetAsync(c->d_small + 64, 0, sizeof(int), c->stream), "status reset");
+      KX_TRY(launch_adj_substep(c, tauk[k], W, tk[k], d_g));
+      KX_TRY(launch_combine(c, 1, 1));   // lambda(t_k) = W w(tau_k)
+    }
+  }
+  KX_TRY(launch_adj_cells(c, d_grad));
+  KX_CUDA(c, cudaMemcpyAsync(c->h_small, d_int, sizeof(double) * nfreq, cudaMemcpyDeviceToHost, c->stream),
+          "loss read");
+  KX_CUDA(c, cudaMemcpyAsync(c->h_small + 128, c->d_small + 64, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+          "status read");
+  KX_TRY(sync(c));
+  int status = 0;
+  std::memcpy(&status, c->h_small + 128, sizeof(int));
+  if (status) return fail(c, KX_ENONFINITE, "adjoint: singular projected exponential");
+  double L = 0.0;
+  for (int f = 0; f < nfreq; ++f) L += c->h_small[f];
+  *loss = L;
   return KX_OK;
 }
 

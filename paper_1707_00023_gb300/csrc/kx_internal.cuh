@@ -127,6 +127,15 @@ struct kx_ctx {
   void* d_tmp;              // one extra vector
   void* d_tmp2;             // one extra vector
   double* d_expm_ws;        // projected exponential workspace
+  // adjoint workspace (max_checkpoints > 0)
+  void* d_ckpt = nullptr;   // max_checkpoints states of the forward solution
+  double* d_adj_Q = nullptr;      // per-E-node time integrals
+  float* d_adj_alpha = nullptr;   // quadrature coefficients
+  float* d_adj_omg = nullptr;
+  float* d_adj_cw = nullptr;
+  float* d_adj_sn = nullptr;
+  double* d_gauss = nullptr;      // Gauss-Legendre nodes and weights on [0, 1]
+  int adj_nq_max = 0;
   void* d_zre;              // stationary parts, max_freqs x n (real)
   void* d_zim;              // stationary parts, max_freqs x n (imaginary)
   kx_stats stats;
@@ -146,9 +155,18 @@ namespace kx {
 kx_status launch_setup_material(kx_ctx* c);
 kx_status launch_apply(kx_ctx* c, const void* v, void* w, int transpose);
 kx_status launch_pass_a(kx_ctx* c, int slot0, int ns, int j, const void* g_aug);
+// pass A with the transposed operator A^T
+kx_status launch_pass_a_tr(kx_ctx* c, int slot0, int ns, int j);
 // pass A reading the per-cell permittivity directly (no 1/eps table)
 kx_status launch_pass_a_cells(kx_ctx* c, int slot, int j, const double* d_eps_cell);
 kx_status launch_pass_b(kx_ctx* c, int slot0, int ns, int j);
+
+// adjoint.cu
+kx_status launch_adj_seed(kx_ctx* c, const void* y, void* lam, int axis, int idx);
+kx_status launch_adj_substep(kx_ctx* c, double tau, double omega, double tk, const void* g);
+kx_status launch_adj_cells(kx_ctx* c, double* grad);
+void gauss_legendre01(int n, double* x, double* w);
+int gauss_points();
 
 // linalg.cu
 kx_status launch_norm_init(kx_ctx* c, int slot0, int ns);

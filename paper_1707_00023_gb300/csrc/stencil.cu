@@ -124,7 +124,7 @@ kx_status launch_apply(kx_ctx* c, const void* v, void* w, int transpose) {
 //   w = A v_j  (v_j = scale[j] * V_j)       [augmented: w = [A y - (a/eta) g; -W b; W a]]
 //   d_i = V_i^T w for i <= j, and ||w||^2, fused in one sweep over the cells.
 // The last block forms H[i, j] = scale[i] * d_i.
-template <typename T, int DIM, int AUG, typename Mat>
+template <typename T, int DIM, int AUG, typename Mat, int TR = 0>
 __global__ void __launch_bounds__(NTHREADS) k_pass_a(Geo g, SlotSet<T> ss, int j, int64_t ld, Mat mat,
                                                     const T* __restrict__ gsrc) {
   constexpr int NC = DIM == 2 ? 3 : 6;
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_a(Geo g, SlotSet<T> ss, int j
     T o[NC];
     if (act) {
       const Cell q = make_cell(g, cell);
-      stencil<T, DIM, 0>(g, vin, mat, q, o);
+      stencil<T, DIM, TR>(g, vin, mat, q, o);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         o[c] *= tsj;
@@ -396,11 +396,11 @@ __global__ void __launch_bounds__(NTHREADS) k_fin_a(SlotSet<float> ss, int j, in
     H[col + (int64_t)j * ldh] = h;
     if (!isfinite(h)) { st->status = KX_ENONFINITE; st->done = 1; }
   } else {
-    if (aug) {
-      augv[2 * (j + 1)] = wa;
-      augv[2 * (j + 1) + 1] = wb;
-      tot += wa * wa + wb * wb;
-    }
+    // the augmented entries of w (zero when the operator is not augmented,
+    // so no stale entries of an earlier augmented run reach pass B)
+    augv[2 * (j + 1)] = wa;
+    augv[2 * (j + 1) + 1] = wb;
+    if (aug) tot += wa * wa + wb * wb;
     const double wn = sqrt(tot);
     if (!isfinite(wn)) { st->status = KX_ENONFINITE; st->done = 1; }
     if (wn > st->wmax) st->wmax = wn;
@@ -473,6 +473,39 @@ static kx_status pass_a_cells_t(kx_ctx* c, int slot, int j, const double* eps) {
   k_fin_a<<<j + 2, NTHREADS, 0, c->stream>>>(make_slotset<float>(c, slot), j, c->m + 1, nb, 0);
   KX_CHECK_LAUNCH(c);
   return KX_OK;
+}
+
+// Pass A of the Arnoldi process for the transposed operator A^T (adjoint
+// problem): same sweep with the transposed stencil.
+template <typename T>
+static kx_status pass_a_tr_t(kx_ctx* c, int slot, int ns, int j) {
+  const Geo& g = c->geo;
+  SlotSet<T> s = make_slotset<T>(c, slot);
+  const TableMat<T> mat{(const T*)c->d_inv_eps, (const T*)c->d_sig2};
+  const int64_t rounds = (g.ncell + NTHREADS - 1) / NTHREADS;
+  static int grid[2] = {0, 0};
+  int& gr = grid[g.dim == 3];
+  if (!gr)
+    gr = persistent_grid(c, g.dim == 2 ? (const void*)k_pass_a<T, 2, 0, TableMat<T>, 1>
+                                       : (const void*)k_pass_a<T, 3, 0, TableMat<T>, 1>, 1 << 30, 0);
+  const int nb = (int)std::min<int64_t>(std::min<int64_t>(rounds, gr), c->ps);
+  const dim3 grd(nb, ns);
+  if (g.dim == 2) k_pass_a<T, 2, 0, TableMat<T>, 1><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr);
+  else k_pass_a<T, 3, 0, TableMat<T>, 1><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr);
+  KX_CHECK_LAUNCH(c);
+  k_fin_a<<<dim3(j + 2, ns), NTHREADS, 0, c->stream>>>(make_slotset<float>(c, slot), j, c->m + 1, nb, 0);
+  KX_CHECK_LAUNCH(c);
+  return KX_OK;
+}
+
+kx_status launch_pass_a_tr(kx_ctx* c, int slot, int ns, int j) {
+  const double vb = (double)c->n * c->esize;
+  const double bytes = (j + 2) * vb + (double)(c->geo.ncomp - c->geo.nh) * c->geo.ncell * c->esize;
+  time_begin(c);
+  const kx_status st = c->d.precision == KX_FP64 ? pass_a_tr_t<double>(c, slot, ns, j)
+                                                 : pass_a_tr_t<float>(c, slot, ns, j);
+  time_end(c, KX_K_PASS_A, bytes * ns);
+  return st;
 }
 
 kx_status launch_pass_a_cells(kx_ctx* c, int slot, int j, const double* d_eps_cell) {

@@ -1,0 +1,83 @@
+"""GPU adjoint: dL/d eps (summed output-plane intensity) against the oracle
+gradient and against central differences of the GPU FP64 forward solve."""
+import numpy as np
+import pytest
+
+import scenario as S
+from oracle import adjoint
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+from paper_1707_00023_gb300 import Context, intensity_loss  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("cfg", ["2d", "3d"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_adjoint_against_oracle_gradient(cfg, prec):
+    sc = S.config_2d(n=10, ndisks=2, T=6.0) if cfg == "2d" else S.config_3d(n=8, fill=0.3, T=6.0)
+    eps = sc.eps_cell * (1.0 + 0.3 * np.random.default_rng(3).random(sc.grid.shape))
+    oms = S.freq_list(2)
+    want = adjoint.grad_adjoint(sc.grid, eps, sc.g, oms, sc.T, sc.plane)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    ctx = Context(sc.grid, eps, precision=prec, krylov_dim=32, max_freqs=2, batch=2, max_checkpoints=64)
+    loss, grad = ctx.adjoint_response_grad(torch.tensor(sc.g, dtype=dt, device="cuda"), oms, sc.T,
+                                           rtol=1e-11 if prec == "fp64" else 1e-7, plane=sc.plane)
+    lw = adjoint.loss(sc.grid, eps, sc.g, oms, sc.T, sc.plane)
+    tol = 1e-8 if prec == "fp64" else 1e-4
+    assert abs(loss - lw) < tol * lw
+    assert rel(grad.cpu().numpy(), want) < (1e-7 if prec == "fp64" else 1e-4)
+    ctx.close()
+
+
+def test_adjoint_fp32_against_central_differences_64_cells():
+    """FP32 adjoint gradient on 64 random cells against central differences
+    (step 1e-3 eps_c, Richardson) of the FP64 GPU forward solve."""
+    sc = S.config_3d(n=16, fill=0.3, T=30.0)
+    oms = S.freq_list(2)
+    eps = sc.eps_cell.copy()
+    ctx = Context(sc.grid, eps, precision="fp32", krylov_dim=48, max_freqs=2, batch=2, max_checkpoints=64)
+    loss, grad = ctx.adjoint_response_grad(torch.tensor(sc.g, dtype=torch.float32, device="cuda"), oms, sc.T,
+                                           rtol=1e-7, plane=sc.plane)
+    ctx.close()
+    f64 = Context(sc.grid, eps, precision="fp64", krylov_dim=48, max_freqs=2, batch=2)
+    g64 = torch.tensor(sc.g, dtype=torch.float64, device="cuda")
+
+    def L(e):
+        f64.set_permittivity(e)
+        return float(f64.response_at_freqs(g64, oms, sc.T, rtol=1e-12, method="plain", plane=sc.plane,
+                                           want_plane=False)["intensity"].sum())
+
+    cells = np.random.default_rng(17).choice(eps.size, 64, replace=False)
+    gflat = grad.cpu().numpy().reshape(-1)
+    fd = []
+    for c in cells:
+        vals = []
+        for h in (1e-3 * eps.reshape(-1)[c], 0.5e-3 * eps.reshape(-1)[c]):
+            ep = eps.copy().reshape(-1); ep[c] += h
+            em = eps.copy().reshape(-1); em[c] -= h
+            vals.append((L(ep) - L(em)) / (2 * h))
+        fd.append((4 * vals[1] - vals[0]) / 3)
+    fd = np.array(fd)
+    f64.close()
+    assert np.abs(gflat[cells] - fd).max() < 1e-4 * np.abs(fd).max()
+
+
+def test_autograd_function():
+    sc = S.config_3d(n=8, fill=0.3, T=6.0)
+    oms = S.freq_list(2)
+    ctx = Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=32, max_freqs=2, batch=2,
+                  max_checkpoints=64)
+    eps = torch.tensor(sc.eps_cell, dtype=torch.float64, device="cuda", requires_grad=True)
+    g = torch.tensor(sc.g, dtype=torch.float64, device="cuda")
+    loss = intensity_loss(ctx, eps, g, oms, sc.T, rtol=1e-11, plane=sc.plane)
+    loss.backward()
+    want = adjoint.grad_adjoint(sc.grid, sc.eps_cell, sc.g, oms, sc.T, sc.plane)
+    assert rel(eps.grad.cpu().numpy(), want) < 1e-7
+    ctx.close()
