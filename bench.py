@@ -48,20 +48,35 @@ WORKLOADS = {
     # 2D 64^2, 40 disks, FP64, m = 30, T = 200, plain method
     "2d64_m30_T200": dict(dim=2, n=64, seed=1708, T=200.0, m=30, nfreq=1, prec="fp64",
                           method="plain", rtol=1e-11, t_oracle=200.0),
-    # 3D 128^3, 32 frequencies in [0.8, 1.2] Omega0, split
+    # 3D 128^3, 32 frequencies in [0.8, 1.2] Omega0 (the multi-frequency batch)
     "3d128_32f_T400": dict(dim=3, n=128, seed=1710, fill=0.3, T=400.0, m=64, nfreq=32,
-                           prec="fp32", method="split", rtol=1e-7, t_oracle=4.0),
+                           prec="fp32", method="plain", rtol=1e-7, t_oracle=4.0, batch=16),
+    # uneven batch: 48 instances, sizes U{32..96}^3, 4 frequencies each, concurrent
+    "uneven48_4f": dict(kind="uneven", count=48, seed=1711, T=400.0, m=64, nfreq=4, prec="fp32",
+                        method="plain", rtol=1e-7, threads=8),
+    # adjoint: 3D 96^3, 8 frequencies, gradient of the summed output-plane intensity
+    "adjoint3d96_8f": dict(kind="adjoint", dim=3, n=96, seed=1712, fill=0.3, T=400.0, m=64, nfreq=8,
+                           prec="fp32", method="plain", rtol=1e-7, checkpoints=128),
 }
 DEFAULT = "3d64_m64_T400_32f"
 
 
-def scenario_for(w):
+def shard_frequencies(nfreq, rank, world, lo=0.8, hi=1.2):
+    """This rank's frequencies: every rank gets nfreq of the world * nfreq
+    frequencies spread over [lo, hi] * Omega0, interleaved (weak scaling; the
+    responses are independent, no data-path collective)."""
+    import scenario as S
+    allf = S.freq_list(nfreq * world, lo, hi)
+    return allf[rank::world]
+
+
+def scenario_for(w, rank=0, world=1):
     import scenario as S
     if w["dim"] == 2:
         sc = S.config_2d(n=w["n"], seed=w["seed"], T=w["T"], m=w["m"])
     else:
         sc = S.config_3d(n=w["n"], seed=w["seed"], fill=w["fill"], T=w["T"], m=w["m"])
-    sc.omegas = S.freq_list(w["nfreq"])
+    sc.omegas = shard_frequencies(w["nfreq"], rank, world) if w["nfreq"] > 1 else S.freq_list(1)
     return sc
 
 
@@ -141,10 +156,12 @@ def dist_setup(n_gpus):
 
 
 def barrier_max(dist, value):
+    """Max of a host value over ranks (CUDA tensor under NCCL, CPU under gloo)."""
     if dist is None:
         return value
     import torch
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -188,6 +205,121 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def timed_steps(args, dist, fn, stream):
+    """W untimed steps, then K steps between barriers and synchronisations,
+    timed by CUDA events on ``stream``; returns (max device ms over ranks,
+    wall s, clocks)."""
+    import torch
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop(int(os.environ.get("LOCAL_RANK", "0")))
+    return barrier_max(dist, ev0.elapsed_time(ev1)), wall, clk
+
+
+def run_uneven(args, w):
+    """Uneven batch: independent instances of different sizes solved
+    concurrently by the native multi-problem driver (one stream per instance)."""
+    import torch
+    import scenario as S
+    from paper_1707_00023_gb300 import Context, response_multi
+
+    rank, world, local, dist = dist_setup(args.gpus)
+    t0 = time.perf_counter()
+    scs = S.config_uneven(count=w["count"], seed=w["seed"] + rank, T=w["T"], m=w["m"], nfreq=w["nfreq"])
+    t_gen = time.perf_counter() - t0
+    dt = torch.float64 if w["prec"] == "fp64" else torch.float32
+    ctxs, gs = [], []
+    for sc in scs:
+        ctxs.append(Context(sc.grid, sc.eps_cell, precision=w["prec"], krylov_dim=w["m"], max_freqs=w["nfreq"],
+                            batch=w["nfreq"], stream="own"))
+        gs.append(torch.tensor(sc.g, dtype=dt, device="cuda"))
+    torch.cuda.synchronize()
+    oms = np.stack([sc.omegas for sc in scs])
+    planes = np.array([sc.plane for sc in scs])
+    main_stream = torch.cuda.current_stream()
+    launches0 = sum(c.stats()["kernel_launches"] for c in ctxs)
+    res = {}
+
+    def step():
+        res["out"] = response_multi(ctxs, gs, oms, w["T"], rtol=w["rtol"], planes=planes, nthreads=w["threads"])
+
+    dev_ms, wall, clk = timed_steps(args, dist, step, main_stream)
+    launches = sum(c.stats()["kernel_launches"] for c in ctxs) - launches0
+    # device events on the current stream do not order the instance streams;
+    # the wall clock around the synchronised call is the job time here
+    job_s = barrier_max(dist, wall)
+    responses = len(scs) * w["nfreq"] * args.steps * world
+    sizes = [sc.grid.n[0] for sc in scs]
+    if rank == 0:
+        line = {"metric": METRIC, "value": responses / job_s, "unit": "responses/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * job_s / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "instances": len(scs), "sizes_min_max": [min(sizes), max(sizes)],
+                           "unknowns_total": int(sum(sc.grid.nunk for sc in scs)), "nfreq_each": w["nfreq"],
+                           "T": w["T"], "krylov_dim": w["m"], "host_threads": w["threads"],
+                           "timing": "wall clock around the synchronised multi-problem call",
+                           "media_generation_s": round(t_gen, 1)},
+                "gpu_launches": launches, "clocks": clk, "roofline": None, "cpu_baseline": None,
+                "e2e": None}
+        print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+
+
+def run_adjoint(args, w):
+    """Gradient of the summed output-plane intensity w.r.t. per-cell eps."""
+    import torch
+    from paper_1707_00023_gb300 import Context
+
+    rank, world, local, dist = dist_setup(args.gpus)
+    sc = scenario_for(w, rank, world)
+    dt = torch.float64 if w["prec"] == "fp64" else torch.float32
+    stream = torch.cuda.Stream()
+    ctx = Context(sc.grid, sc.eps_cell, precision=w["prec"], krylov_dim=w["m"], max_freqs=w["nfreq"],
+                  batch=2, stream=stream, max_checkpoints=w["checkpoints"])
+    g = torch.tensor(sc.g, dtype=dt, device="cuda")
+    torch.cuda.synchronize()
+    res = {}
+
+    def step():
+        with torch.cuda.stream(stream):
+            res["loss"], res["grad"] = ctx.adjoint_response_grad(g, sc.omegas, w["T"], rtol=w["rtol"],
+                                                                 plane=sc.plane)
+
+    dev_ms, wall, clk = timed_steps(args, dist, step, stream)
+    st = ctx.stats()
+    if rank == 0:
+        grads = args.steps * world
+        line = {"metric": "gradients/s of the summed output-plane intensity (8 frequencies) w.r.t. per-cell eps",
+                "value": grads / (dev_ms / 1000.0), "unit": "gradients/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "grid": list(sc.grid.n), "nfreq": w["nfreq"], "T": w["T"],
+                           "krylov_dim": w["m"]},
+                "loss": res["loss"], "grad_norm": float(res["grad"].norm()), "clocks": clk,
+                "stats": st, "cpu_baseline": None, "e2e": None, "roofline": None}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -200,12 +332,16 @@ def main():
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
+    if w.get("kind") == "uneven":
+        return run_uneven(args, w)
+    if w.get("kind") == "adjoint":
+        return run_adjoint(args, w)
 
     import torch
     from paper_1707_00023_gb300 import Context
 
     rank, world, local, dist = dist_setup(args.gpus)
-    sc = scenario_for(w)
+    sc = scenario_for(w, rank, world)
     dt = torch.float64 if w["prec"] == "fp64" else torch.float32
     stream = torch.cuda.Stream()
     ctx = Context(sc.grid, sc.eps_cell, precision=w["prec"], krylov_dim=w["m"],

@@ -86,10 +86,15 @@ typedef struct {
   int64_t kernel_launches; /* kernels this library launched               */
 } kx_stats;
 
+/* Pass as cuda_stream to have the context create (and destroy) its own
+ * non-blocking stream; kx_stream() returns it. */
+#define KX_OWN_STREAM ((void*)-1)
+
 /* Create a context.  eps_cell: HOST array of n[0]*n[1](*n[2]) per-cell
  * relative permittivities (> 0, finite), x fastest; mu_r = 1 (Sect. 2.1).
  * The permittivity of an E node is the mean over the cells whose closure
- * holds the node.  stream: a cudaStream_t (NULL = legacy default stream).
+ * holds the node.  stream: a cudaStream_t (NULL = legacy default stream) or
+ * KX_OWN_STREAM.
  * All workspace (batch Krylov bases of krylov_dim + 1 vectors, projected
  * matrices, reduction buffers) is allocated here.
  * Errors: KX_EINVAL (descriptor), KX_ENONFINITE (eps), KX_ENOMEM. */
@@ -98,6 +103,9 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell,
 
 /* Release a context and its workspace.  NULL is accepted. */
 kx_status krylov_expm_destroy(kx_ctx* ctx);
+
+/* The CUDA stream the context works on (a cudaStream_t). */
+void* kx_stream(const kx_ctx* ctx);
 
 /* Number of unknowns n (including wall nodes) of the context's grid. */
 int64_t kx_num_unknowns(const kx_ctx* ctx);
@@ -202,6 +210,22 @@ kx_status adjoint_response_grad(kx_ctx* ctx, const void* d_g, const double* omeg
 /* Replace the per-cell permittivity of a context (host or device array of
  * ncell doubles, each > 0); the grid and workspace stay.  Synchronises. */
 kx_status kx_set_permittivity(kx_ctx* ctx, const double* eps_cell);
+
+/* Independent problems in one call (the uneven batch: many scatterer
+ * instances of different sizes).  ctxs[i] holds problem i's grid, medium and
+ * CUDA stream (use a distinct non-default stream per context); d_g[i] its
+ * source; omegas is nctx x nfreq (row i = problem i's frequencies); planes is
+ * nctx x 2; intensity and err_est (host, nctx x nfreq, or NULL) as for
+ * response_at_freqs.  nthreads host threads take the problems largest-first
+ * and drive them concurrently, so their kernels overlap on the GPU (each
+ * context's sub-steps replay a captured CUDA graph).  The streams of the
+ * contexts must be distinct (KX_OWN_STREAM guarantees it).  Each context must be
+ * created with max_freqs >= nfreq; its batch sets how many of its frequencies
+ * advance together.  On failure the first error is returned and its text is
+ * kx_last_error(NULL). */
+kx_status response_at_freqs_multi(kx_ctx* const* ctxs, int nctx, const void* const* d_g,
+                                  const double* omegas, int nfreq, double T, double rtol, int method,
+                                  const int* planes, double* intensity, double* err_est, int nthreads);
 
 /* Counters; kx_reset_stats zeroes them. */
 kx_status kx_get_stats(const kx_ctx* ctx, kx_stats* out);

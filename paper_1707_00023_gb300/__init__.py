@@ -6,7 +6,7 @@ in-tree by ``paper_1707_00023_gb300.build``; this package only marshals
 arguments.
 """
 from ._binding import (KX_FP32, KX_FP64, KX_PEC, KX_PERIODIC, KX_PLAIN, KX_SPLIT, Context,
-                       KxError, EXPORTS, intensity_loss, load_library)
+                       KxError, EXPORTS, intensity_loss, load_library, response_multi)
 
-__all__ = ["Context", "KxError", "load_library", "intensity_loss", "EXPORTS", "KX_FP32", "KX_FP64", "KX_PEC",
+__all__ = ["Context", "KxError", "load_library", "intensity_loss", "response_multi", "EXPORTS", "KX_FP32", "KX_FP64", "KX_PEC",
            "KX_PERIODIC", "KX_PLAIN", "KX_SPLIT"]

@@ -26,7 +26,7 @@ EXPORTS = ["krylov_expm_create", "krylov_expm_destroy", "kx_num_unknowns", "appl
            "arnoldi", "expm_phi_project", "stationary_solve", "expm_action",
            "response_at_freqs", "kx_get_stats", "kx_reset_stats", "kx_set_timing",
            "kx_kernel_times", "kx_last_error", "kx_arnoldi_noalloc", "kx_noalloc_last_error",
-           "adjoint_response_grad", "kx_set_permittivity"]
+           "adjoint_response_grad", "kx_set_permittivity", "response_at_freqs_multi", "kx_stream"]
 KCLASSES = ["pass_a", "pass_b", "restart", "projected", "zupdate", "apply"]
 
 
@@ -71,6 +71,8 @@ def load_library(path: Optional[str] = None):
     lib.krylov_expm_destroy.argtypes = [vp]
     lib.kx_num_unknowns.argtypes = [vp]
     lib.kx_num_unknowns.restype = ctypes.c_int64
+    lib.kx_stream.argtypes = [vp]
+    lib.kx_stream.restype = vp
     lib.apply_A.argtypes = [vp, vp, vp, ctypes.c_int]
     lib.arnoldi.argtypes = [vp, vp, ctypes.c_int, vp, vp, dp, ip]
     lib.expm_phi_project.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -85,6 +87,9 @@ def load_library(path: Optional[str] = None):
     lib.adjoint_response_grad.argtypes = [vp, vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                           ip, vp, dp]
     lib.kx_set_permittivity.argtypes = [vp, vp]
+    lib.response_at_freqs_multi.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp), dp,
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ip,
+                                            dp, dp, ctypes.c_int]
     lib.kx_set_timing.argtypes = [vp, ctypes.c_int]
     lib.kx_kernel_times.argtypes = [vp, ctypes.POINTER(KernelTime)]
     lib.kx_last_error.argtypes = [vp]
@@ -93,7 +98,7 @@ def load_library(path: Optional[str] = None):
     lib.kx_noalloc_last_error.argtypes = []
     lib.kx_noalloc_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("kx_num_unknowns", "kx_last_error", "kx_noalloc_last_error"):
+        if name not in ("kx_num_unknowns", "kx_last_error", "kx_noalloc_last_error", "kx_stream"):
             getattr(lib, name).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -110,7 +115,9 @@ class Context:
     ``grid`` is any object with attributes dim, n, bc, layer_axis,
     layer_cells, sigma_max (e.g. ``scenario.Grid``).  ``eps_cell`` is the
     per-cell permittivity (numpy, x fastest).  ``stream``: a torch CUDA
-    stream (default: the current stream).
+    stream (default: the current stream), or ``"own"`` for a private stream
+    created by the library (distinct per context; use it for concurrent
+    problems, since torch hands out streams from a small pool).
     """
 
     def __init__(self, grid, eps_cell, precision: str = "fp32", krylov_dim: int = 64,
@@ -135,15 +142,18 @@ class Context:
         d.max_checkpoints = max_checkpoints
         self.desc = d
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
-        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        own = isinstance(stream, str) and stream == "own"
+        self.stream = None if own else (stream if stream is not None else torch.cuda.current_stream())
         eps = np.ascontiguousarray(np.asarray(eps_cell, np.float64).reshape(-1))
         h = ctypes.c_void_p()
-        st = self.lib.krylov_expm_create(ctypes.byref(d), _dptr(eps),
-                                         ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        sarg = ctypes.c_void_p(-1) if own else ctypes.c_void_p(self.stream.cuda_stream)
+        st = self.lib.krylov_expm_create(ctypes.byref(d), _dptr(eps), sarg, ctypes.byref(h))
         if st != KX_OK:
             raise KxError(st, self.lib.kx_last_error(None).decode())
         self.h = h
         self.n = int(self.lib.kx_num_unknowns(h))
+        if own:
+            self.stream = torch.cuda.ExternalStream(int(self.lib.kx_stream(h)))
 
     # -- helpers -----------------------------------------------------------
     def _check(self, st):
@@ -315,3 +325,27 @@ def intensity_loss(ctx, eps_cell, g, omegas, T, rtol=1e-8, plane=(0, 0)):
             return gout * grad.to(gout.device)
 
     return _IntensityLoss.apply(eps_cell)
+
+
+def response_multi(ctxs, gs, omegas, T, rtol=1e-8, method="plain", planes=None, nthreads=8):
+    """Independent problems concurrently (``response_at_freqs_multi``).
+
+    ctxs: Contexts (distinct non-default streams); gs: their source tensors;
+    omegas: (nctx, nfreq) array; planes: (nctx, 2).  Returns (intensity,
+    err_est), each (nctx, nfreq)."""
+    lib = load_library()
+    n = len(ctxs)
+    om = np.ascontiguousarray(np.asarray(omegas, np.float64).reshape(n, -1))
+    nf = om.shape[1]
+    pl = np.ascontiguousarray(np.asarray(planes, np.int32).reshape(n, 2))
+    hs = (ctypes.c_void_p * n)(*[c.h for c in ctxs])
+    gp = (ctypes.c_void_p * n)(*[c._vec(g, "g").value for c, g in zip(ctxs, gs)])
+    inten = np.zeros((n, nf))
+    err = np.zeros((n, nf))
+    st = lib.response_at_freqs_multi(hs, n, gp, _dptr(om), nf, float(T), float(rtol),
+                                     KX_SPLIT if method == "split" else KX_PLAIN,
+                                     pl.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(inten), _dptr(err),
+                                     int(nthreads))
+    if st != KX_OK:
+        raise KxError(st, lib.kx_last_error(None).decode())
+    return inten, err

@@ -20,6 +20,8 @@
 #include <vector>
 
 #include "kx_dense.cuh"
+#include <atomic>
+
 #include "kx_internal.cuh"
 
 namespace kx {
@@ -318,7 +320,7 @@ kx_status launch_adj_substep(kx_ctx* c, double tau, double omega, double tk, con
     return KX_EINVAL;
   }
   const int m = c->m;
-  static int attr = 0;
+  static std::atomic<int> attr{0};
   if (!attr) {
     cudaFuncSetAttribute(k_adj_coeffs, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)expm_smem_bytes(MMAX + 2));

@@ -3,8 +3,12 @@
 // library's kernels; the host only sequences launches on the context's
 // stream and reads back small status records.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <numeric>
+#include <thread>
 #include <vector>
 
 #include "kx_internal.cuh"
@@ -103,14 +107,71 @@ kx_status read_states(kx_ctx* c, int slot0, int ns) {
 // of slots [slot0, slot0 + ns) advance together to their final times by
 // sub-steps x <- V_m exp(-t H_m) beta e_1; a slot that has arrived retires and
 // every later kernel skips it.
+// One sub-step's launches: m Arnoldi steps, the projected step control, the
+// combination.
+kx_status substep_launches(kx_ctx* c, int slot0, int ns, const void* g_aug) {
+  KX_TRY(arnoldi_steps(c, slot0, ns, c->m, g_aug));
+  KX_TRY(launch_substep_control(c, slot0, ns));
+  return launch_combine(c, slot0, ns);
+}
+
+// A CUDA graph of one sub-step's launches (all parameters are fixed for the
+// sub-steps of one time_loop; the changing state lives in device memory).
+struct SubstepGraph {
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+  ~SubstepGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+kx_status capture_substep(kx_ctx* c, int slot0, int ns, const void* g_aug, SubstepGraph* out) {
+  const kx_stats saved = c->stats;   // capturing executes nothing: restore the counters
+  const int64_t before = c->stats.kernel_launches;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return KX_ECUDA;
+  }
+  const kx_status st = substep_launches(c, slot0, ns, g_aug);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (st != KX_OK || e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return KX_ECUDA;
+  }
+  const cudaError_t e2 = cudaGraphInstantiate(&out->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) {
+    cudaGetLastError();
+    out->exec = nullptr;
+    return KX_ECUDA;
+  }
+  out->launches = c->stats.kernel_launches - before;
+  c->stats = saved;
+  return KX_OK;
+}
+
 kx_status time_loop(kx_ctx* c, int slot0, int ns, const void* g_aug, double* err_est) {
   KX_TRY(launch_norm_init(c, slot0, ns));
   const int max_sub = 20000;
   bool all = false;
+  // the first sub-step runs eagerly (one-time kernel set-up), the rest replay
+  // a captured graph; capture is skipped on the legacy stream and while the
+  // per-kernel timing is on
+  bool use_graph = c->stream != nullptr && !c->timing;
+  SubstepGraph graph;
   for (int it = 0; it < max_sub && !all; ++it) {
-    KX_TRY(arnoldi_steps(c, slot0, ns, c->m, g_aug));
-    KX_TRY(launch_substep_control(c, slot0, ns));
-    KX_TRY(launch_combine(c, slot0, ns));
+    if (use_graph && it >= 1 && !graph.exec && capture_substep(c, slot0, ns, g_aug, &graph) != KX_OK)
+      use_graph = false;
+    if (use_graph && graph.exec) {
+      KX_CUDA(c, cudaGraphLaunch(graph.exec, c->stream), "sub-step graph launch");
+      c->stats.kernel_launches += graph.launches;
+      c->stats.arnoldi_steps += (int64_t)c->m * ns;
+      c->stats.matvecs += (int64_t)c->m * ns;
+    } else {
+      KX_TRY(substep_launches(c, slot0, ns, g_aug));
+    }
     KX_TRY(read_states(c, slot0, ns));
     all = true;
     for (int q = 0; q < ns; ++q) {
@@ -242,7 +303,16 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
   if (!c) return fail(nullptr, KX_ENOMEM, "host allocation failed");
   c->d = d;
   if (d.dim == 2) c->d.n[2] = 1;
-  c->stream = (cudaStream_t)cuda_stream;
+  if (cuda_stream == KX_OWN_STREAM) {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return fail(nullptr, KX_ECUDA, "stream creation failed");
+    }
+    c->own_stream = true;
+  } else {
+    c->stream = (cudaStream_t)cuda_stream;
+  }
   Geo& g = c->geo;
   g.dim = d.dim;
   g.nx = d.n[0];
@@ -387,11 +457,14 @@ kx_status krylov_expm_destroy(kx_ctx* c) {
     if (p) cudaFree(p);
   if (c->h_state) cudaFreeHost(c->h_state);
   if (c->h_small) cudaFreeHost(c->h_small);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return KX_OK;
 }
 
 int64_t kx_num_unknowns(const kx_ctx* c) { return c ? c->n : 0; }
+
+void* kx_stream(const kx_ctx* c) { return c ? (void*)c->stream : nullptr; }
 
 kx_status apply_A(kx_ctx* c, const void* d_v, void* d_w, int transpose) {
   if (!c) return KX_EINVAL;
@@ -710,6 +783,65 @@ kx_status adjoint_response_grad(kx_ctx* c, const void* d_g, const double* omegas
   double L = 0.0;
   for (int f = 0; f < nfreq; ++f) L += c->h_small[f];
   *loss = L;
+  return KX_OK;
+}
+
+// Independent problems solved concurrently: a pool of host threads takes
+// the contexts largest-first from a shared counter; each context runs on its
+// own stream, so the kernels of different problems overlap on the GPU.
+kx_status response_at_freqs_multi(kx_ctx* const* ctxs, int nctx, const void* const* d_g,
+                                  const double* omegas, int nfreq, double T, double rtol, int method,
+                                  const int* planes, double* intensity, double* err_est, int nthreads) {
+  if (!ctxs || nctx < 1 || !d_g || !omegas || !planes || nfreq < 1) {
+    g_create_err = "response_at_freqs_multi: bad argument";
+    return KX_EINVAL;
+  }
+  for (int i = 0; i < nctx; ++i)
+    if (!ctxs[i]) {
+      g_create_err = "response_at_freqs_multi: NULL context";
+      return KX_EINVAL;
+    }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    g_create_err = "response_at_freqs_multi: no CUDA device";
+    return KX_ECUDA;
+  }
+  std::vector<int> order(nctx);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ctxs[a]->n > ctxs[b]->n; });
+  std::atomic<int> next{0};
+  std::atomic<int> first_err{KX_OK};
+  std::mutex mu;
+  std::string err_text;
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= nctx || first_err.load() != KX_OK) return;
+      const int i = order[k];
+      const kx_status st = response_at_freqs(ctxs[i], d_g[i], omegas + (size_t)i * nfreq, nfreq, T, rtol, method,
+                                             planes + 2 * i, nullptr, intensity ? intensity + (size_t)i * nfreq : nullptr,
+                                             err_est ? err_est + (size_t)i * nfreq : nullptr, nullptr);
+      if (st != KX_OK) {
+        int expect = KX_OK;
+        if (first_err.compare_exchange_strong(expect, st)) {
+          std::lock_guard<std::mutex> lk(mu);
+          err_text = std::string("problem ") + std::to_string(i) + ": " + ctxs[i]->err;
+        }
+        return;
+      }
+    }
+  };
+  const int nt = std::max(1, std::min(nthreads, nctx));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& th : pool) th.join();
+  if (first_err.load() != KX_OK) {
+    g_create_err = err_text;
+    return (kx_status)first_err.load();
+  }
   return KX_OK;
 }
 

@@ -96,6 +96,7 @@ struct Material {
 struct kx_ctx {
   kx_desc d;
   cudaStream_t stream;
+  bool own_stream = false;   // created by (and destroyed with) the context
   kx::Geo geo;
   int64_t n;        // unknowns
   int64_t ld;       // stride between stored basis columns

@@ -3,6 +3,8 @@
 // of the stationary parts, residual norms and the output-plane response.
 // All reductions are deterministic: per-block partials in a fixed order,
 // summed by the last block to finish.
+#include <atomic>
+
 #include "kx_internal.cuh"
 #include "kx_reduce.cuh"
 
@@ -137,13 +139,13 @@ kx_status launch_pass_b(kx_ctx* c, int slot, int ns, int j) {
   const int aug = 1;  // augmented entries are zero when unused
   time_begin(c);
   struct End { kx_ctx* c; int j, ns; ~End() { time_end(c, KX_K_PASS_B, (j + 3.0) * c->n * c->esize * ns); } } end{c, j, ns};
-  static int grid[2] = {0, 0};
+  static std::atomic<int> grid[2];
   const int fp64 = c->d.precision == KX_FP64;
   if (!grid[fp64])
     grid[fp64] = persistent_grid(c, fp64 ? (const void*)k_pass_b<double> : (const void*)k_pass_b<float>,
                                  1 << 30, 0);
   const int64_t rounds = (c->n / (fp64 ? 2 : 4) + NTHREADS - 1) / NTHREADS;
-  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(rounds, grid[fp64]), c->ps));
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(rounds, grid[fp64].load()), c->ps));
   if (fp64) {
     k_pass_b<double><<<dim3(nb, ns), NTHREADS, 0, c->stream>>>(make_slotset<double>(c, slot), j, c->n, c->ld,
                                                               ldh, aug, 1e-12);
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(NTHREADS) k_zupdate(const T* __restrict__ V, i
 
 kx_status launch_zupdate(kx_ctx* c, int slot, int nfreq, void* zre, void* zim, int m) {
   const size_t sm = (size_t)2 * nfreq * MMAX * c->esize;
-  static int attr_done = 0;
+  static std::atomic<int> attr_done{0};
   if (!attr_done) {
     cudaFuncSetAttribute(k_zupdate<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(2 * MAXF * MMAX * sizeof(double)));

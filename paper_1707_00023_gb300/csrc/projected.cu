@@ -6,6 +6,8 @@
 //  * projected solutions with a sine source (eq. (corr2), Corollary 1),
 //  * shifted Hessenberg solves of the multi-shift FOM.
 // Matrices live in shared memory, row-major, leading dimension = size.
+#include <atomic>
+
 #include "kx_internal.cuh"
 #include "kx_dense.cuh"
 
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(256) k_substep(SlotSet<float> ss, int ldh, int
 kx_status launch_substep_control(kx_ctx* c, int slot, int ns) {
   const int m = c->m;
   const size_t sm = expm_smem_bytes(m);
-  static int attr_done = 0;
+  static std::atomic<int> attr_done{0};
   if (!attr_done) {
     cudaFuncSetAttribute(k_substep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)expm_smem_bytes(MMAX + 2));
     attr_done = 1;
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(256) k_expm_project(const double* H, int ldh, 
 kx_status launch_expm_project(kx_ctx* c, const double* dH, int ldh, int m, double beta, double tau,
                               const double* d_om, int nfreq, double* d_u) {
   const int n = nfreq > 0 ? m + 2 : m;
-  static int attr_done = 0;
+  static std::atomic<int> attr_done{0};
   if (!attr_done) {
     cudaFuncSetAttribute(k_expm_project, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)expm_smem_bytes(MMAX + 2));
@@ -308,7 +310,7 @@ kx_status launch_shifted_solve(kx_ctx* c, int slot, int nfreq, int m) {
   Slot<double> s = make_slot<double>(c, slot);
   int* status = reinterpret_cast<int*>(c->d_small + 64);
   const size_t sm = (size_t)m * m * sizeof(cplx);
-  static int attr_done = 0;
+  static std::atomic<int> attr_done{0};
   if (!attr_done) {
     cudaFuncSetAttribute(k_shifted<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(MMAX * MMAX * sizeof(cplx)));
     cudaFuncSetAttribute(k_shifted<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(MMAX * MMAX * sizeof(cplx)));

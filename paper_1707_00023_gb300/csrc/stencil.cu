@@ -7,6 +7,8 @@
 // backward-difference curl of H on the E nodes.  One thread owns one cell
 // (all 3 or 6 components of that cell), which keeps the neighbour planes of
 // a block close in time and the reuse inside L1/L2.
+#include <atomic>
+
 #include "kx_internal.cuh"
 #include "kx_reduce.cuh"
 #include "kx_stencil.cuh"
@@ -421,9 +423,9 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int ns, int j, const void* gaug) 
                     ((uintptr_t)gaug % 16) == 0;
   const int64_t items = vec4 ? g.ncell / 4 : g.ncell;
   const int64_t rounds = (items + NTHREADS - 1) / NTHREADS;
-  static int grid[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  static std::atomic<int> grid[3][2];
   const int kind = vec4 ? 2 : (g.dim == 3);
-  int& gr = grid[kind][gaug != nullptr];
+  std::atomic<int>& gr = grid[kind][gaug != nullptr];
   if (!gr) {
     const void* fn;
     if (vec4) fn = gaug ? (const void*)k_pass_a4<1> : (const void*)k_pass_a4<0>;
@@ -431,7 +433,7 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int ns, int j, const void* gaug) 
     else fn = gaug ? (const void*)k_pass_a<T, 3, 1, TableMat<T>> : (const void*)k_pass_a<T, 3, 0, TableMat<T>>;
     gr = persistent_grid(c, fn, 1 << 30, 0);
   }
-  const int nb = (int)std::min<int64_t>(std::min<int64_t>(rounds, gr), c->ps);
+  const int nb = (int)std::min<int64_t>(std::min<int64_t>(rounds, gr.load()), c->ps);
   const dim3 grd(nb, ns);
   if (vec4) {
     SlotSet<float> sf = make_slotset<float>(c, slot);
@@ -461,12 +463,12 @@ static kx_status pass_a_cells_t(kx_ctx* c, int slot, int j, const double* eps) {
   SlotSet<T> s = make_slotset<T>(c, slot);
   const CellMat<T> mat{eps, c->d.sigma_max, c->d.layer_cells};
   const int64_t rounds = (g.ncell + NTHREADS - 1) / NTHREADS;
-  static int grid[2] = {0, 0};
-  int& gr = grid[g.dim == 3];
+  static std::atomic<int> grid[2];
+  std::atomic<int>& gr = grid[g.dim == 3];
   if (!gr)
     gr = persistent_grid(c, g.dim == 2 ? (const void*)k_pass_a<T, 2, 0, CellMat<T>>
                                        : (const void*)k_pass_a<T, 3, 0, CellMat<T>>, 1 << 30, 0);
-  const int nb = (int)std::min<int64_t>(std::min<int64_t>(rounds, gr), c->ps);
+  const int nb = (int)std::min<int64_t>(std::min<int64_t>(rounds, gr.load()), c->ps);
   if (g.dim == 2) k_pass_a<T, 2, 0, CellMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr);
   else k_pass_a<T, 3, 0, CellMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr);
   KX_CHECK_LAUNCH(c);
@@ -483,12 +485,12 @@ static kx_status pass_a_tr_t(kx_ctx* c, int slot, int ns, int j) {
   SlotSet<T> s = make_slotset<T>(c, slot);
   const TableMat<T> mat{(const T*)c->d_inv_eps, (const T*)c->d_sig2};
   const int64_t rounds = (g.ncell + NTHREADS - 1) / NTHREADS;
-  static int grid[2] = {0, 0};
-  int& gr = grid[g.dim == 3];
+  static std::atomic<int> grid[2];
+  std::atomic<int>& gr = grid[g.dim == 3];
   if (!gr)
     gr = persistent_grid(c, g.dim == 2 ? (const void*)k_pass_a<T, 2, 0, TableMat<T>, 1>
                                        : (const void*)k_pass_a<T, 3, 0, TableMat<T>, 1>, 1 << 30, 0);
-  const int nb = (int)std::min<int64_t>(std::min<int64_t>(rounds, gr), c->ps);
+  const int nb = (int)std::min<int64_t>(std::min<int64_t>(rounds, gr.load()), c->ps);
   const dim3 grd(nb, ns);
   if (g.dim == 2) k_pass_a<T, 2, 0, TableMat<T>, 1><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr);
   else k_pass_a<T, 3, 0, TableMat<T>, 1><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr);

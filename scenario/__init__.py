@@ -136,7 +136,7 @@ class Scenario:
 
 
 def _place_disks_2d(rng: PCG32, n: int, region, count, rmin, rmax, gap,
-                    max_reject=100000):
+                    max_reject=2000):
     (xlo, xhi), (ylo, yhi) = region
     disks = []
     rejects = 0
@@ -173,7 +173,7 @@ def _raster_disks(n, disks, eps_in, eps_bg):
 
 
 def _place_spheres_3d(rng: PCG32, n, zlo, zhi, fill, rmin, rmax, eps_choices,
-                      eps_bg, gap, max_reject=100000):
+                      eps_bg, gap, max_reject=2000):
     """Random sequential addition of spheres, periodic in x and y.
 
     Stops once the rasterised fill fraction of the slab zlo <= z < zhi reaches
@@ -188,24 +188,35 @@ def _place_spheres_3d(rng: PCG32, n, zlo, zhi, fill, rmin, rmax, eps_choices,
     rejects = 0
     overlap_from = None
     c = np.arange(n) + 0.5
+    batch = 1
     while filled < fill * slab_cells:
-        r = rng.uniform(rmin, rmax)
-        cx = rng.uniform(0.0, n)
-        cy = rng.uniform(0.0, n)
-        cz = rng.uniform(zlo + r, zhi - r)
-        e_in = eps_choices[rng.randint(0, len(eps_choices) - 1)] if len(eps_choices) > 1 else eps_choices[0]
-        ok = True
+        # candidates are drawn in batches; the first one that overlaps no
+        # placed sphere is accepted and the rest of the batch is discarded
+        cand = []
+        for _ in range(batch):
+            r = rng.uniform(rmin, rmax)
+            cx = rng.uniform(0.0, n)
+            cy = rng.uniform(0.0, n)
+            cz = rng.uniform(zlo + r, zhi - r)
+            e_in = eps_choices[rng.randint(0, len(eps_choices) - 1)] if len(eps_choices) > 1 else eps_choices[0]
+            cand.append((r, cx, cy, cz, e_in))
+        cb = np.array([q[:4] for q in cand])
         if rejects < max_reject and len(radii):
-            d = centres - np.array([cx, cy, cz])
-            d[:, 0] -= n * np.round(d[:, 0] / n)
-            d[:, 1] -= n * np.round(d[:, 1] / n)
-            dist = np.sqrt((d * d).sum(1))
-            ok = bool(np.all(dist >= radii + r + gap))
-        elif rejects >= max_reject and overlap_from is None:
-            overlap_from = len(spheres)
-        if not ok:
-            rejects += 1
+            d = centres[None, :, :] - cb[:, None, 1:4]
+            d[:, :, 0] -= n * np.round(d[:, :, 0] / n)
+            d[:, :, 1] -= n * np.round(d[:, :, 1] / n)
+            dist = np.sqrt((d * d).sum(2))
+            ok = np.all(dist >= radii[None, :] + cb[:, 0:1] + gap, axis=1)
+        else:
+            if rejects >= max_reject and overlap_from is None:
+                overlap_from = len(spheres)
+            ok = np.ones(batch, bool)
+        if not ok.any():
+            rejects += batch
+            batch = min(2 * batch, 64)      # near jamming: test more candidates at once
             continue
+        r, cx, cy, cz, e_in = cand[int(np.argmax(ok))]
+        batch = max(1, batch // 2)
         rejects = 0
         centres = np.vstack([centres, [cx, cy, cz]])
         radii = np.append(radii, r)
@@ -214,16 +225,21 @@ def _place_spheres_3d(rng: PCG32, n, zlo, zhi, fill, rmin, rmax, eps_choices,
         k0 = max(int(math.floor(cz - r)), 0)
         k1 = min(int(math.ceil(cz + r)), n)
         dz = c[k0:k1] - cz
-        dx = c - cx
+        # bounding box in x and y, indices wrapped periodically
+        ix = np.arange(int(math.floor(cx - r)), int(math.ceil(cx + r)) + 1) % n
+        iy = np.arange(int(math.floor(cy - r)), int(math.ceil(cy + r)) + 1) % n
+        ix, iy = np.unique(ix), np.unique(iy)
+        dx = c[ix] - cx
         dx -= n * np.round(dx / n)
-        dy = c - cy
+        dy = c[iy] - cy
         dy -= n * np.round(dy / n)
         inside = (dz[:, None, None] ** 2 + dy[None, :, None] ** 2
                   + dx[None, None, :] ** 2) < r * r
-        sub = eps[k0:k1]
+        sub = eps[k0:k1][:, iy][:, :, ix]
         newly = inside & (sub == eps_bg)
         filled += int(newly.sum())
         sub[inside] = e_in
+        eps[k0:k1, iy[:, None], ix[None, :]] = sub
     return eps, spheres, overlap_from
 
 
@@ -360,4 +376,17 @@ def uneven_batch(count=48, seed=1711, nmin=32, nmax=96):
         e = 2.25 if rng.randint(0, 1) == 0 else 4.0
         f = rng.uniform(0.2, 0.4)
         out.append((n, e, f, seed * 1000 + b))
+    return out
+
+
+def config_uneven(count=48, seed=1711, nmin=32, nmax=96, T=400.0, m=64, nfreq=4):
+    """The uneven batch: ``count`` 3D instances with cubic sizes U{nmin..nmax},
+    inclusion permittivity from {2.25, 4}, fill U[0.2, 0.4], each with
+    ``nfreq`` frequencies in [0.9, 1.1] * OMEGA0."""
+    out = []
+    for (n, e, f, s) in uneven_batch(count, seed, nmin, nmax):
+        sc = config_3d(n=n, seed=s, fill=f, T=T, m=m, eps_choices=(e,))
+        sc.omegas = OMEGA0 * np.linspace(0.9, 1.1, nfreq)
+        sc.name = f"uneven_n{n}_e{e}_f{f:.2f}"
+        out.append(sc)
     return out

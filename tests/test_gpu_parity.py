@@ -331,3 +331,50 @@ def test_full_size_3d64_T400_fp32_vs_fp64():
     ctx.close()
     for f in range(2):
         assert rel(a["Y"][f].double().cpu().numpy(), b["Y"][f].cpu().numpy()) < 1e-6
+
+
+def test_graph_replayed_substeps_match_eager():
+    """On a non-default stream the time sub-steps replay a captured CUDA
+    graph; results equal the eager launches on the default stream."""
+    sc = S.config_3d(n=12, fill=0.3, T=30.0)
+    oms = S.freq_list(3)
+    outs = []
+    for stream in (None, torch.cuda.Stream()):
+        ctx = Context(sc.grid, sc.eps_cell, precision="fp32", krylov_dim=24, max_freqs=3, batch=3,
+                      stream=stream)
+        with torch.cuda.stream(stream or torch.cuda.current_stream()):
+            g = dev(sc.g, torch.float32)
+            out = ctx.response_at_freqs(g, oms, sc.T, rtol=1e-7, method="plain", plane=sc.plane,
+                                        want_full=True)
+        torch.cuda.synchronize()
+        outs.append((out["Y"].cpu().numpy(), ctx.stats()))
+        ctx.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1]["kernel_launches"] == outs[1][1]["kernel_launches"]
+    assert outs[0][1]["substeps"] == outs[1][1]["substeps"]
+
+
+def test_multi_problem_driver_uneven_sizes():
+    """Independent problems of different sizes in one call, driven by host
+    threads on separate streams: intensities equal those of one call per
+    problem, and the oracle's."""
+    from paper_1707_00023_gb300 import response_multi
+    scs = S.config_uneven(count=4, seed=5, nmin=8, nmax=14, T=15.0, m=24, nfreq=2)
+    ctxs, gs = [], []
+    for sc in scs:
+        ctxs.append(Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=24, max_freqs=2, batch=2,
+                            stream="own"))
+        gs.append(dev(sc.g, torch.float64))
+    torch.cuda.synchronize()
+    oms = np.stack([sc.omegas for sc in scs])
+    planes = np.array([sc.plane for sc in scs])
+    inten, err = response_multi(ctxs, gs, oms, 15.0, rtol=1e-11, planes=planes, nthreads=3)
+    for i, sc in enumerate(scs):
+        one = ctxs[i].response_at_freqs(gs[i], sc.omegas, 15.0, rtol=1e-11, method="plain", plane=sc.plane)
+        np.testing.assert_array_equal(one["intensity"], inten[i])
+    sc = scs[0]
+    A = yee.Operator(sc.grid, sc.eps_cell).matrix()
+    want = yee.intensity(sc.grid, exact.y_plain(A, sc.g, sc.omegas[1], 15.0), sc.plane)
+    assert abs(inten[0, 1] - want) < 1e-9 * want
+    for c in ctxs:
+        c.close()
