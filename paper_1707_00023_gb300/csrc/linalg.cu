@@ -167,6 +167,19 @@ kx_status launch_pass_b(kx_ctx* c, int slot, int ns, int j) {
 // u_i scale_i V_i first (the Krylov update y = V_m u, eq. (corr2) /
 // (upd1)); in the augmented case the phase entries are then reset to their
 // exact values eta (sin W t, cos W t).
+// Error-free compensated combination (FP32 path): every coefficient is a
+// float pair hi + lo of its FP64 value, each product's rounding error comes
+// from an FMA and each sum's from Knuth's TwoSum, so the result is the
+// correctly summed combination up to the final rounding.
+__device__ __forceinline__ void acc_comp(float& s, float& c, float hi, float lo, float v) {
+  const float p = hi * v;
+  const float e = fmaf(hi, v, -p) + lo * v;
+  const float t = s + p;
+  const float z = t - s;
+  c += ((s - (t - z)) + (p - z)) + e;
+  s = t;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS) k_restart(SlotSet<T> ss, int64_t n, int64_t ld, int mode) {
   using V4 = typename Vec<T>::t;
@@ -174,10 +187,15 @@ __global__ void __launch_bounds__(NTHREADS) k_restart(SlotSet<T> ss, int64_t n, 
   const Slot<T> s = slot_at(ss, blockIdx.y);
   if (s.st->retired) return;
   __shared__ T coef[MMAX];
+  __shared__ float coef_lo[MMAX];
   int m = 0;
   if (mode == 1) {
     m = s.st->m_done;
-    for (int q = threadIdx.x; q < m; q += blockDim.x) coef[q] = (T)(s.u[q] * s.scale[q]);
+    for (int q = threadIdx.x; q < m; q += blockDim.x) {
+      const double cf = s.u[q] * s.scale[q];
+      coef[q] = (T)cf;
+      coef_lo[q] = (float)(cf - (double)(T)cf);
+    }
   }
   __syncthreads();
   T* __restrict__ y = s.V;
@@ -186,7 +204,36 @@ __global__ void __launch_bounds__(NTHREADS) k_restart(SlotSet<T> ss, int64_t n, 
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
        q += (int64_t)gridDim.x * blockDim.x) {
     V4 x;
-    if (mode == 1) {
+    if (mode == 1 && sizeof(T) == 4) {
+      const float4* __restrict__ Vf = reinterpret_cast<const float4*>(s.V);
+      const int64_t ldv = ld / 4;
+      float sx = 0.f, sy = 0.f, sz = 0.f, sw = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, cw = 0.f;
+      int col = 0;
+      for (; col + 4 <= m; col += 4) {
+        float4 v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) v[t] = Vf[(int64_t)(col + t) * ldv + q];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const float hi = (float)coef[col + t], lo = coef_lo[col + t];
+          acc_comp(sx, cx, hi, lo, v[t].x);
+          acc_comp(sy, cy, hi, lo, v[t].y);
+          acc_comp(sz, cz, hi, lo, v[t].z);
+          acc_comp(sw, cw, hi, lo, v[t].w);
+        }
+      }
+      for (; col < m; ++col) {
+        const float4 v = Vf[(int64_t)col * ldv + q];
+        const float hi = (float)coef[col], lo = coef_lo[col];
+        acc_comp(sx, cx, hi, lo, v.x);
+        acc_comp(sy, cy, hi, lo, v.y);
+        acc_comp(sz, cz, hi, lo, v.z);
+        acc_comp(sw, cw, hi, lo, v.w);
+      }
+      const float4 r = make_float4(sx + cx, sy + cy, sz + cz, sw + cw);
+      x = *reinterpret_cast<const V4*>(&r);
+      reinterpret_cast<V4*>(y)[q] = x;
+    } else if (mode == 1) {
       const V4* __restrict__ Vv = reinterpret_cast<const V4*>(s.V);
       const int64_t ldv = ld / W;
       V4 x1 = vzero<T>();
