@@ -19,6 +19,9 @@ arXiv:1707.00023 it follows):
                   routes: the augmented homogeneous system and the
                   asymptotic splitting of eq. (split1); the stationary part
                   z_stat = (A + i Omega I)^{-1} g.
+* ``restart``  -- residual-based restarting in Krylov dimension with one
+                  basis per restart for every frequency (Sect. 3.4,
+                  eq. (rst), Corollary 2, Fig. alg:rst).
 * ``adjoint``  -- gradient of the output-plane intensity with respect to
                   per-cell permittivity (no counterpart in the paper).
 
