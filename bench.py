@@ -45,6 +45,11 @@ WORKLOADS = {
                                    prec="fp32", method="plain", rtol=1e-7, t_oracle=20.0, batch=8),
     "3d64_m64_T400_32f": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=32,
                               prec="fp32", method="plain", rtol=1e-7, t_oracle=20.0, batch=32),
+    # the same 32 frequencies by restart in Krylov dimension: one basis per
+    # restart for all of them (Corollary 2, Fig. alg:rst)
+    "3d64_m64_T400_32f_rst": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=32,
+                                  prec="fp32", method="rstdim", rtol=1e-7, t_oracle=20.0, rst_samples=4096,
+                                  batch=2),
     # 2D 64^2, 40 disks, FP64, m = 30, T = 200, plain method
     "2d64_m30_T200": dict(dim=2, n=64, seed=1708, T=200.0, m=30, nfreq=1, prec="fp64",
                           method="plain", rtol=1e-11, t_oracle=200.0),
@@ -345,7 +350,8 @@ def main():
     dt = torch.float64 if w["prec"] == "fp64" else torch.float32
     stream = torch.cuda.Stream()
     ctx = Context(sc.grid, sc.eps_cell, precision=w["prec"], krylov_dim=w["m"],
-                  max_freqs=w["nfreq"], batch=w.get("batch", 1), stream=stream)
+                  max_freqs=w["nfreq"], batch=w.get("batch", 1), stream=stream,
+                  rst_samples=w.get("rst_samples", 0))
     g_host = torch.tensor(sc.g, dtype=dt).pin_memory()
     g = g_host.to("cuda")
     torch.cuda.synchronize()
@@ -443,18 +449,23 @@ def main():
         ref = ctx64.response_at_freqs(g64, oms[pick], w["T"], rtol=1e-11, method="plain", plane=sc.plane,
                                       want_full=True)
     stream.synchronize()
-    errs = []
+    errs, perrs = [], []
     for q, f in enumerate(pick):
         a = full["Y"][f].double().cpu().numpy()
         b = ref["Y"][q].cpu().numpy()
         errs.append(float(np.linalg.norm(a - b) / np.linalg.norm(b)))
+        pa = full["E_plane"][f].double().cpu().numpy()
+        pb = ref["E_plane"][q].cpu().numpy()
+        perrs.append(float(np.linalg.norm(pa - pb) / np.linalg.norm(pb)))
     acc["rel_l2_field_vs_fp64"] = dict(zip([int(f) for f in pick], errs))
+    acc["rel_l2_plane_E_vs_fp64"] = dict(zip([int(f) for f in pick], perrs))
     acc["max_rel_l2"] = max(errs)
+    acc["max_rel_l2_plane_E"] = max(perrs)
     ctx64.close()
     single = None
-    if w.get("batch", 1) > 1:
+    if w.get("batch", 1) > 1 or w["method"] == "rstdim":
         ctx1 = Context(sc.grid, sc.eps_cell, precision=w["prec"], krylov_dim=w["m"], max_freqs=1,
-                       batch=1, stream=stream)
+                       batch=1, stream=stream, rst_samples=w.get("rst_samples", 0))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):

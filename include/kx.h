@@ -51,7 +51,7 @@ typedef enum {
 
 enum { KX_PERIODIC = 0, KX_PEC = 1 };
 enum { KX_FP64 = 0, KX_FP32 = 1 };
-enum { KX_PLAIN = 0, KX_SPLIT = 1 };
+enum { KX_PLAIN = 0, KX_SPLIT = 1, KX_RSTDIM = 2 };
 
 /* Problem descriptor.  Grid of n[0] x n[1] (x n[2]) unit cells; the
  * absorbing layer (conductivity ramping linearly from 0 to sigma_max over
@@ -72,6 +72,10 @@ typedef struct {
   int batch;          /* bases held for concurrent transients, >= 1          */
   int max_checkpoints; /* forward states kept for the adjoint (0: no adjoint;
                           otherwise batch >= 2); one per time sub-step       */
+  int rst_samples;    /* time samples of [0, T] per frequency kept by the
+                         restart-in-dimension method (0: method unavailable);
+                         the workspace is max_freqs * rst_samples * 72
+                         bytes plus max_freqs output-plane accumulators      */
 } kx_desc;
 
 typedef struct kx_ctx kx_ctx;
@@ -175,6 +179,8 @@ kx_status expm_action(kx_ctx* ctx, const void* d_y0, double T, double rtol,
  *   method KX_SPLIT: eq. (split1) with all stationary parts from one
  *     shifted solve (stationary_solve) and the transients exp(-TA) Im z_j by
  *     expm_action (Fig. alg:spl1 steps 1-3 for each frequency).
+ *   method KX_RSTDIM: response_restart_dim with dt_sample = 0 and
+ *     max_restarts = 0; err_est receives its resid.
  *   plane: host int[2] = {axis, index}: output plane perpendicular to axis.
  *   d_E_plane: device, nfreq x nE x (plane nodes) scalars (nE = 1 in 2D:
  *     Ez; 3 in 3D: Ex, Ey at the plane, Ez half a cell above), or NULL.
@@ -186,6 +192,44 @@ kx_status response_at_freqs(kx_ctx* ctx, const void* d_g, const double* omegas,
                             int nfreq, double T, double rtol, int method,
                             const int* plane, void* d_E_plane, double* intensity,
                             double* err_est, void* d_Y);
+
+/* Frequency responses by residual-based restarting in Krylov dimension
+ * (Sect. 3.4, eq. (rst), Corollary 2, Fig. alg:rst; regular Krylov
+ * variant).  One Arnoldi basis per restart serves every frequency: restart 1
+ * starts from g / ||g|| with source alpha(t) = ||g|| sin(omega_j t); after m
+ * steps each frequency's projected problem u' = -H_m u + alpha(t) e_1,
+ * u(0) = 0 (eq. (corr2)) is integrated over [0, T], y_j(T) += V_m u(T)
+ * (eq. (upd1)), and the residual alphahat(t) v_{m+1}, alphahat =
+ * -h_{m+1,m} e_m^T u(t) (eq. (resid)), is the next restart's source, from
+ * v_{m+1}.  alphahat is stored per frequency at Nt + 1 equally spaced times
+ * with its first two derivatives (Fig. alg:rst step 2(b)); the projected
+ * problems are integrated exactly for the quintic Hermite interpolant of
+ * those samples on each sample interval (matrix exponential and phi
+ * functions of the interval, FP64).
+ *   rtol       : frequency j stops after the restart whose new residual has
+ *                max_t |alphahat(t)| <= rtol * ||g|| (step 2(c)); rtol = 0
+ *                runs max_restarts restarts.
+ *   dt_sample  : sample spacing (T / Nt rounds it down to fit); 0 picks
+ *                T * ||H_m||_1 / Nt = 1 (KX_FP32) or 0.3 (KX_FP64) from the
+ *                first restart's Hessenberg matrix.
+ *   max_restarts: cap (0: 3 * T * ||H_m||_1 / m + 20).
+ *   plane, d_E_plane, intensity, d_Y: as for response_at_freqs.  The plane
+ *                values are accumulated in FP64 over the restarts; d_Y in
+ *                KX_FP32 through a compensated float pair.
+ *   resid      : host nfreq (or NULL): last max_t |alphahat(t)| / ||g||.
+ *   restarts   : host nfreq (or NULL): restarts each frequency took.
+ * Needs a context with rst_samples >= Nt (KX_EINVAL names the Nt needed);
+ * krylov_dim = 64 is advised, smaller m lets intermediate residuals grow.
+ * With batch >= 2 the projected work of restart k runs on an auxiliary
+ * stream of the context while restart k+1's Arnoldi process runs on the
+ * context's stream (so one Arnoldi process may run past the last restart);
+ * results are the same bits as with batch = 1.
+ * Synchronises the stream.  KX_ENOCONV (with the iterate) when a frequency
+ * has not stopped after max_restarts restarts. */
+kx_status response_restart_dim(kx_ctx* ctx, const void* d_g, const double* omegas, int nfreq,
+                               double T, double rtol, double dt_sample, int max_restarts,
+                               const int* plane, void* d_E_plane, double* intensity,
+                               double* resid, int* restarts, void* d_Y);
 
 /* Gradient of the summed output-plane intensity
  *     L = sum_j sum_plane |E_j(T)|^2,   E_j from response_at_freqs(KX_PLAIN),
@@ -244,7 +288,8 @@ enum { KX_K_PASS_A = 0,    /* operator application fused with the Gram-Schmidt d
        KX_K_PROJ = 3,      /* FP64 projected work (expm, step control, shifted solves) */
        KX_K_ZUPDATE = 4,   /* multi-shift update of the stationary parts            */
        KX_K_APPLY = 5,     /* plain operator application                            */
-       KX_NKCLASS = 6 };
+       KX_K_CASCADE = 6,   /* projected time stepping of restart in dimension       */
+       KX_NKCLASS = 7 };
 typedef struct {
   double ms;
   double bytes;

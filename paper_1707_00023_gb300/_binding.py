@@ -18,7 +18,8 @@ LIBPATH = os.path.join(HERE, "libkx.so")
 KX_OK, KX_EINVAL, KX_ENOMEM, KX_ECUDA, KX_ENONFINITE, KX_ENOCONV, KX_ETIMEOUT = range(7)
 KX_PERIODIC, KX_PEC = 0, 1
 KX_FP64, KX_FP32 = 0, 1
-KX_PLAIN, KX_SPLIT = 0, 1
+KX_PLAIN, KX_SPLIT, KX_RSTDIM = 0, 1, 2
+METHODS = {"plain": KX_PLAIN, "split": KX_SPLIT, "rstdim": KX_RSTDIM}
 STATUS_NAMES = {0: "KX_OK", 1: "KX_EINVAL", 2: "KX_ENOMEM", 3: "KX_ECUDA",
                 4: "KX_ENONFINITE", 5: "KX_ENOCONV", 6: "KX_ETIMEOUT"}
 
@@ -26,8 +27,9 @@ EXPORTS = ["krylov_expm_create", "krylov_expm_destroy", "kx_num_unknowns", "appl
            "arnoldi", "expm_phi_project", "stationary_solve", "expm_action",
            "response_at_freqs", "kx_get_stats", "kx_reset_stats", "kx_set_timing",
            "kx_kernel_times", "kx_last_error", "kx_arnoldi_noalloc", "kx_noalloc_last_error",
-           "adjoint_response_grad", "kx_set_permittivity", "response_at_freqs_multi", "kx_stream"]
-KCLASSES = ["pass_a", "pass_b", "restart", "projected", "zupdate", "apply"]
+           "adjoint_response_grad", "kx_set_permittivity", "response_at_freqs_multi", "kx_stream",
+           "response_restart_dim"]
+KCLASSES = ["pass_a", "pass_b", "restart", "projected", "zupdate", "apply", "cascade"]
 
 
 class KxError(RuntimeError):
@@ -41,7 +43,7 @@ class Desc(ctypes.Structure):
                 ("layer_axis", ctypes.c_int), ("layer_cells", ctypes.c_int),
                 ("sigma_max", ctypes.c_double), ("precision", ctypes.c_int),
                 ("krylov_dim", ctypes.c_int), ("max_freqs", ctypes.c_int), ("batch", ctypes.c_int),
-                ("max_checkpoints", ctypes.c_int)]
+                ("max_checkpoints", ctypes.c_int), ("rst_samples", ctypes.c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -82,6 +84,8 @@ def load_library(path: Optional[str] = None):
     lib.expm_action.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, vp, dp]
     lib.response_at_freqs.argtypes = [vp, vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int, ip, vp, dp, dp, vp]
+    lib.response_restart_dim.argtypes = [vp, vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, ip, vp, dp, dp, ip, vp]
     lib.kx_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.kx_reset_stats.argtypes = [vp]
     lib.adjoint_response_grad.argtypes = [vp, vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -118,10 +122,13 @@ class Context:
     stream (default: the current stream), or ``"own"`` for a private stream
     created by the library (distinct per context; use it for concurrent
     problems, since torch hands out streams from a small pool).
+    ``rst_samples``: time samples per frequency held for the restart-in-
+    dimension method (``method="rstdim"``; 0 leaves it unavailable).
     """
 
     def __init__(self, grid, eps_cell, precision: str = "fp32", krylov_dim: int = 64,
-                 max_freqs: int = 1, batch: int = 1, stream=None, max_checkpoints: int = 0):
+                 max_freqs: int = 1, batch: int = 1, stream=None, max_checkpoints: int = 0,
+                 rst_samples: int = 0):
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -140,6 +147,7 @@ class Context:
         d.max_freqs = max_freqs
         d.batch = batch
         d.max_checkpoints = max_checkpoints
+        d.rst_samples = rst_samples
         self.desc = d
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         own = isinstance(stream, str) and stream == "own"
@@ -273,12 +281,35 @@ class Context:
         pl = (ctypes.c_int * 2)(int(plane[0]), int(plane[1]))
         st = self.lib.response_at_freqs(
             self.h, self._vec(g, "g"), _dptr(om), nf, float(T), float(rtol),
-            KX_SPLIT if method == "split" else KX_PLAIN, pl,
+            METHODS[method], pl,
             ctypes.c_void_p(Ep.data_ptr()) if Ep is not None else None, _dptr(inten), _dptr(err),
             ctypes.c_void_p(Y.data_ptr()) if Y is not None else None)
         if not (allow_noconv and st == KX_ENOCONV):
             self._check(st)
         return {"E_plane": Ep, "intensity": inten, "err_est": err, "Y": Y, "status": st}
+
+    def response_restart_dim(self, g, omegas, T, rtol=1e-8, dt_sample=0.0, max_restarts=0, plane=(0, 0),
+                             want_plane=True, want_full=False, allow_noconv=False):
+        """Responses by restarting in Krylov dimension (``response_restart_dim``).
+
+        Returns E_plane, intensity, the last relative residual maxima and
+        the restarts each frequency took."""
+        om = np.ascontiguousarray(np.asarray(omegas, np.float64))
+        nf = len(om)
+        nE, npl = self.plane_size(plane)
+        Ep = self._torch.empty((nf, nE, npl), dtype=self.dtype, device="cuda") if want_plane else None
+        Y = self.empty(nf) if want_full else None
+        inten = np.zeros(nf)
+        res = np.zeros(nf)
+        rst = np.zeros(nf, np.int32)
+        pl = (ctypes.c_int * 2)(int(plane[0]), int(plane[1]))
+        st = self.lib.response_restart_dim(
+            self.h, self._vec(g, "g"), _dptr(om), nf, float(T), float(rtol), float(dt_sample), int(max_restarts),
+            pl, ctypes.c_void_p(Ep.data_ptr()) if Ep is not None else None, _dptr(inten), _dptr(res),
+            rst.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.c_void_p(Y.data_ptr()) if Y is not None else None)
+        if not (allow_noconv and st == KX_ENOCONV):
+            self._check(st)
+        return {"E_plane": Ep, "intensity": inten, "resid": res, "restarts": rst, "Y": Y, "status": st}
 
     def set_permittivity(self, eps_cell):
         """Replace the per-cell permittivity (numpy array or CUDA float64 tensor)."""
@@ -343,7 +374,7 @@ def response_multi(ctxs, gs, omegas, T, rtol=1e-8, method="plain", planes=None, 
     inten = np.zeros((n, nf))
     err = np.zeros((n, nf))
     st = lib.response_at_freqs_multi(hs, n, gp, _dptr(om), nf, float(T), float(rtol),
-                                     KX_SPLIT if method == "split" else KX_PLAIN,
+                                     METHODS[method],
                                      pl.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(inten), _dptr(err),
                                      int(nthreads))
     if st != KX_OK:

@@ -198,6 +198,20 @@ kx_status check_vec(kx_ctx* c, const void* p, const char* name) {
   return KX_OK;
 }
 
+// Output plane {axis, index}: validated, and its node count (all E components).
+kx_status check_plane(kx_ctx* c, const int* plane, int* axis, int* idx, int64_t* P) {
+  if (!plane) return fail(c, KX_EINVAL, "plane is NULL");
+  *axis = plane[0];
+  *idx = plane[1];
+  if (*axis < 0 || *axis >= c->d.dim) return fail(c, KX_EINVAL, "bad plane axis");
+  const int na = *axis == 0 ? c->geo.nx : (*axis == 1 ? c->geo.ny : c->geo.nz);
+  if (*idx < 0 || *idx >= na) return fail(c, KX_EINVAL, "bad plane index");
+  int a = 0, b = 0;
+  plane_dims(c->geo, *axis, &a, &b);
+  *P = (int64_t)(c->geo.ncomp - c->geo.nh) * a * b;
+  return KX_OK;
+}
+
 kx_status check_omegas(kx_ctx* c, const double* om, int nfreq) {
   if (nfreq < 1 || nfreq > c->d.max_freqs)
     return fail(c, KX_EINVAL, "nfreq out of range 1..max_freqs");
@@ -293,6 +307,7 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
   if (d.batch < 1 || d.batch > 64) return fail(nullptr, KX_EINVAL, "batch must be 1..64");
   if (d.max_checkpoints < 0 || (d.max_checkpoints > 0 && d.batch < 2))
     return fail(nullptr, KX_EINVAL, "max_checkpoints must be >= 0, and the adjoint needs batch >= 2");
+  if (d.rst_samples < 0 || d.rst_samples > (1 << 24)) return fail(nullptr, KX_EINVAL, "rst_samples must be 0 .. 2^24");
   const int nz = d.dim == 3 ? d.n[2] : 1;
   const int64_t ncell = (int64_t)d.n[0] * d.n[1] * nz;
   for (int64_t i = 0; i < ncell; ++i)
@@ -412,6 +427,41 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
       return fail(nullptr, KX_ECUDA, std::string("Gauss nodes upload failed: ") + cudaGetErrorString(e));
     }
   }
+  if (d.rst_samples > 0) {
+    int na = 0, nb = 0;
+    int64_t pmax = 0;
+    for (int a = 0; a < d.dim; ++a) {
+      plane_dims(g, a, &na, &nb);
+      pmax = std::max<int64_t>(pmax, (int64_t)na * nb);
+    }
+    c->rst_plane_max = (int64_t)(g.ncomp - g.nh) * pmax;
+    Alloc rst[] = {
+        {(void**)&c->d_rst_b, (size_t)d.max_freqs * d.rst_samples * RST_P * sizeof(double)},
+        {(void**)&c->d_rst_smp, (size_t)d.max_freqs * (d.rst_samples + 1) * 3 * sizeof(double)},
+        {(void**)&c->d_rst_mats, (size_t)RST_MATS * sizeof(double)},
+        {(void**)&c->d_rst_u, (size_t)MAXF * MMAX * sizeof(double)},
+        {(void**)&c->d_rst_res, (size_t)MAXF * sizeof(double)},
+        {(void**)&c->d_rst_state, (size_t)MAXF * sizeof(int)},
+        {(void**)&c->d_rst_yp, (size_t)d.max_freqs * c->rst_plane_max * sizeof(double)},
+    };
+    for (auto& a : rst) {
+      e = cudaMalloc(a.p, a.bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        krylov_expm_destroy(c);
+        return fail(nullptr, KX_ENOMEM, std::string("restart workspace allocation failed: ") + cudaGetErrorString(e));
+      }
+    }
+    e = cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_arnoldi, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_proj[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_proj[1], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      krylov_expm_destroy(c);
+      return fail(nullptr, KX_ECUDA, std::string("auxiliary stream creation failed: ") + cudaGetErrorString(e));
+    }
+  }
   e = cudaMallocHost((void**)&c->h_state, (size_t)B * sizeof(SlotState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_small, 256 * sizeof(double));
   if (e != cudaSuccess) {
@@ -452,11 +502,19 @@ kx_status krylov_expm_destroy(kx_ctx* c) {
                   c->d_part, c->d_counter, c->d_u, c->d_state, c->d_rho, c->d_coef, c->d_coefd,
                   c->d_omegas, c->d_small, c->d_tmp, c->d_tmp2, c->d_expm_ws, c->d_zre, c->d_zim,
                   c->d_ckpt, c->d_adj_Q, c->d_adj_alpha, c->d_adj_omg, c->d_adj_cw, c->d_adj_sn,
-                  c->d_gauss};
+                  c->d_gauss, c->d_rst_b, c->d_rst_smp, c->d_rst_mats, c->d_rst_u, c->d_rst_res,
+                  c->d_rst_state, c->d_rst_yp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_state) cudaFreeHost(c->h_state);
   if (c->h_small) cudaFreeHost(c->h_small);
+  if (c->aux_stream) {
+    cudaStreamSynchronize(c->aux_stream);
+    cudaStreamDestroy(c->aux_stream);
+  }
+  if (c->ev_arnoldi) cudaEventDestroy(c->ev_arnoldi);
+  for (cudaEvent_t ev : c->ev_proj)
+    if (ev) cudaEventDestroy(ev);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return KX_OK;
@@ -583,6 +641,9 @@ kx_status response_at_freqs(kx_ctx* c, const void* d_g, const double* omegas, in
   KX_TRY(check_vec(c, d_g, "d_g"));
   KX_TRY(check_omegas(c, omegas, nfreq));
   if (!(T > 0.0) || !std::isfinite(T) || !(rtol > 0.0)) return fail(c, KX_EINVAL, "bad T or rtol");
+  if (method == KX_RSTDIM)
+    return response_restart_dim(c, d_g, omegas, nfreq, T, rtol, 0.0, 0, plane, d_E_plane, intensity, err_est,
+                                nullptr, d_Y);
   if (method != KX_PLAIN && method != KX_SPLIT) return fail(c, KX_EINVAL, "bad method");
   if (!plane) return fail(c, KX_EINVAL, "plane is NULL");
   const int axis = plane[0], idx = plane[1];
@@ -658,6 +719,169 @@ kx_status response_at_freqs(kx_ctx* c, const void* d_g, const double* omegas, in
   }
   KX_TRY(sync(c));
   if (conv != KX_OK) return fail(c, conv, "stationary solve did not reach its tolerance");
+  return KX_OK;
+}
+
+kx_status response_restart_dim(kx_ctx* c, const void* d_g, const double* omegas, int nfreq, double T,
+                               double rtol, double dt_sample, int max_restarts, const int* plane,
+                               void* d_E_plane, double* intensity, double* resid, int* restarts, void* d_Y) {
+  if (!c) return KX_EINVAL;
+  KX_TRY(check_vec(c, d_g, "d_g"));
+  KX_TRY(check_omegas(c, omegas, nfreq));
+  if (c->d.rst_samples <= 0) return fail(c, KX_EINVAL, "context created with rst_samples = 0");
+  if (!(T > 0.0) || !std::isfinite(T)) return fail(c, KX_EINVAL, "T must be finite and > 0");
+  if (!(rtol >= 0.0) || !std::isfinite(rtol)) return fail(c, KX_EINVAL, "rtol must be finite and >= 0");
+  if (!(dt_sample >= 0.0) || !std::isfinite(dt_sample)) return fail(c, KX_EINVAL, "dt_sample must be finite and >= 0");
+  if (max_restarts < 0) return fail(c, KX_EINVAL, "max_restarts must be >= 0");
+  int axis = 0, idx = 0;
+  int64_t P = 0;
+  KX_TRY(check_plane(c, plane, &axis, &idx, &P));
+  cudaStream_t A = c->stream;
+  // with two basis slots the projected work of restart k (auxiliary stream)
+  // overlaps the Arnoldi process of restart k + 1 (context stream); per-kernel
+  // timing records on the context stream, so it runs everything there
+  const bool ovl = c->d.batch >= 2 && !c->timing;
+  cudaStream_t Bs = ovl ? c->aux_stream : A;
+  // the cascade (one CTA per frequency) and the set-up CTA stay resident
+  // beside the Arnoldi passes; their grids leave room for them (in both
+  // modes: the grid fixes the order of the reductions, so the bits agree)
+  struct SideCtas {
+    kx_ctx* c;
+    ~SideCtas() { c->side_ctas = 0; }
+  } side{c};
+  c->side_ctas = nfreq + 1;
+  const size_t vbytes = (size_t)c->n * c->esize;
+  // restart 1 starts from v_1 = g / ||g|| in slot 0
+  KX_CUDA(c, cudaMemcpyAsync(slot_col(c, 0, 0), d_g, vbytes, cudaMemcpyDeviceToDevice, A), "copy g");
+  if (ovl) KX_TRY(upload_state(c, 1, fresh_state()));
+  KX_TRY(upload_state(c, 0, fresh_state()));
+  KX_TRY(launch_norm_init(c, 0, 1));
+  SlotState st;
+  KX_TRY(read_state(c, 0, &st));
+  const double beta = st.beta;
+  if (!std::isfinite(beta)) return fail(c, KX_ENONFINITE, "g is not finite");
+  KX_CUDA(c, cudaMemsetAsync(c->d_rst_yp, 0, (size_t)nfreq * P * sizeof(double), A), "zero plane");
+  KX_CUDA(c, cudaMemsetAsync(c->d_rst_state, 0, (size_t)nfreq * sizeof(int), A), "zero states");
+  if (d_Y) {
+    KX_CUDA(c, cudaMemsetAsync(d_Y, 0, (size_t)nfreq * vbytes, A), "zero Y");
+    if (c->d.precision == KX_FP32)
+      KX_CUDA(c, cudaMemsetAsync(c->d_zre, 0, (size_t)nfreq * vbytes, A), "zero Y low parts");
+  }
+  double* d_int = c->d_small + 128;
+  std::vector<int> rcount(nfreq, 0);
+  if (beta == 0.0) {
+    // y = 0: every output is zero
+    KX_TRY(launch_rst_out(c, A, nfreq, P, d_E_plane, d_int, nullptr));
+    KX_TRY(sync(c));
+    for (int f = 0; f < nfreq; ++f) {
+      if (intensity) intensity[f] = 0.0;
+      if (resid) resid[f] = 0.0;
+      if (restarts) restarts[f] = 0;
+    }
+    return KX_OK;
+  }
+  KX_CUDA(c, cudaMemcpyAsync(c->d_omegas, omegas, sizeof(double) * nfreq, cudaMemcpyHostToDevice, A),
+          "omega upload");
+  KX_TRY(arnoldi_steps(c, 0, 1, c->m, nullptr));
+  KX_TRY(read_state(c, 0, &st));
+  if (st.status) return fail(c, (kx_status)st.status, "non-finite value in the Arnoldi process");
+  // sample grid from ||H_m||_1 of the first restart
+  const int ldh = c->m + 1;
+  std::vector<double> Hh((size_t)ldh * c->m);
+  KX_CUDA(c, cudaMemcpyAsync(Hh.data(), make_slot<double>(c, 0).H, Hh.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost, A), "H read");
+  KX_TRY(sync(c));
+  double nu = 0.0;
+  for (int col = 0; col < st.m_done; ++col) {
+    double sum = 0.0;
+    for (int r = 0; r <= std::min(col + 1, st.m_done - 1); ++r) sum += std::fabs(Hh[r + (size_t)col * ldh]);
+    nu = std::max(nu, sum);
+  }
+  if (!std::isfinite(nu)) return fail(c, KX_ENONFINITE, "non-finite Hessenberg matrix");
+  const double per_unit = c->d.precision == KX_FP64 ? 0.3 : 1.0;
+  double want = dt_sample > 0.0 ? T / dt_sample : T * nu / per_unit;
+  want = std::max(1.0, std::ceil(want - 1e-9 * want));
+  if (want > (double)c->d.rst_samples) {
+    char msg[160];
+    snprintf(msg, sizeof(msg), "T needs %.0f time samples; the context holds rst_samples = %d", want,
+             c->d.rst_samples);
+    return fail(c, KX_EINVAL, msg);
+  }
+  const int Nt = (int)want;
+  const double d = T / Nt;
+  const int kmax = max_restarts > 0 ? max_restarts
+                                    : (int)std::min(100000.0, 3.0 * T * nu / c->m + 20.0);
+  double* b = c->d_rst_b;
+  KX_TRY(launch_rst_source(c, A, nfreq, beta, Nt, d, b));
+  const double tol_abs = rtol * beta;
+  bool all_stopped = false;
+  int* h_states = reinterpret_cast<int*>(c->h_small);
+  int* h_status = reinterpret_cast<int*>(c->h_small + 96);
+  if (ovl) KX_CUDA(c, cudaEventRecord(c->ev_arnoldi, A), "event record");
+  for (int k = 1;; ++k) {
+    const int sl = ovl ? (k - 1) & 1 : 0;
+    // projected work of restart k (Fig. alg:rst steps (2), (3))
+    if (ovl) KX_CUDA(c, cudaStreamWaitEvent(Bs, c->ev_arnoldi, 0), "event wait");
+    KX_CUDA(c, cudaMemsetAsync(c->d_small + 64, 0, sizeof(int), Bs), "status reset");
+    KX_TRY(launch_rst_setup(c, Bs, sl, d));
+    KX_TRY(launch_rst_cascade(c, Bs, nfreq, b, Nt, d, tol_abs));
+    KX_TRY(launch_rst_plane(c, Bs, sl, nfreq, axis, idx, P));
+    if (d_Y) KX_TRY(launch_rst_full(c, Bs, sl, nfreq, d_Y));
+    KX_TRY(launch_rst_coef(c, Bs, nfreq, b, Nt, d));
+    c->stats.expm_evals += 1;
+    if (ovl) {
+      KX_CUDA(c, cudaEventRecord(c->ev_proj[sl], Bs), "event record");
+      // restart k + 1's Arnoldi process in the other slot, started before
+      // restart k's stopping test is known (step (1) of the next pass)
+      if (k < kmax) {
+        const int nx = sl ^ 1;
+        if (k >= 2) KX_CUDA(c, cudaStreamWaitEvent(A, c->ev_proj[nx], 0), "event wait");
+        KX_TRY(launch_rst_nextvec(c, A, sl, nx));
+        KX_TRY(launch_norm_init(c, nx, 1));
+        KX_TRY(arnoldi_steps(c, nx, 1, c->m, nullptr));
+        KX_CUDA(c, cudaEventRecord(c->ev_arnoldi, A), "event record");
+      }
+    }
+    KX_CUDA(c, cudaMemcpyAsync(h_states, c->d_rst_state, sizeof(int) * nfreq, cudaMemcpyDeviceToHost, Bs),
+            "state read");
+    KX_CUDA(c, cudaMemcpyAsync(h_status, c->d_small + 64, sizeof(int), cudaMemcpyDeviceToHost, Bs),
+            "status read");
+    KX_CUDA(c, cudaStreamSynchronize(Bs), "stream synchronise");
+    if (*h_status) {
+      sync(c);
+      return fail(c, KX_ENONFINITE, "restart set-up: non-finite Arnoldi process or projected exponential");
+    }
+    all_stopped = true;
+    for (int f = 0; f < nfreq; ++f) {
+      if (h_states[f] == 3) {
+        sync(c);
+        return fail(c, KX_ENONFINITE, "non-finite residual in the projected problem");
+      }
+      if (h_states[f] == 0 || h_states[f] == 1) rcount[f] = k;
+      all_stopped = all_stopped && h_states[f] != 0;
+    }
+    if (all_stopped || k >= kmax) break;
+    if (!ovl) {
+      // the next basis starts from v_{m+1} (same slot, column m_done -> 0)
+      KX_TRY(launch_rst_nextvec(c, A, 0, 0));
+      KX_TRY(launch_norm_init(c, 0, 1));
+      KX_TRY(arnoldi_steps(c, 0, 1, c->m, nullptr));
+    }
+  }
+  if (ovl) KX_CUDA(c, cudaStreamWaitEvent(A, c->ev_proj[0], 0), "event wait");
+  if (ovl) KX_CUDA(c, cudaStreamWaitEvent(A, c->ev_proj[1], 0), "event wait");
+  KX_TRY(launch_rst_out(c, A, nfreq, P, d_E_plane, d_int, d_Y));
+  KX_CUDA(c, cudaMemcpyAsync(c->h_small, d_int, sizeof(double) * nfreq, cudaMemcpyDeviceToHost, A),
+          "intensity read");
+  KX_CUDA(c, cudaMemcpyAsync(c->h_small + 64, c->d_rst_res, sizeof(double) * nfreq, cudaMemcpyDeviceToHost, A),
+          "residual read");
+  KX_TRY(sync(c));
+  for (int f = 0; f < nfreq; ++f) {
+    if (intensity) intensity[f] = c->h_small[f];
+    if (resid) resid[f] = c->h_small[64 + f] / beta;
+    if (restarts) restarts[f] = rcount[f];
+  }
+  if (!all_stopped) return fail(c, KX_ENOCONV, "restart in Krylov dimension: max_restarts reached");
   return KX_OK;
 }
 

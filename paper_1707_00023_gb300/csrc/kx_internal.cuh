@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <cstdio>
@@ -86,6 +87,43 @@ __host__ __device__ __forceinline__ Slot<T> slot_at(const SlotSet<T>& ss, int y)
   return s;
 }
 
+// Output plane perpendicular to `axis` at index `idx`: its nodes are
+// t = q * (na * nb) + a + na * b, q the E component and (a, b) the two
+// in-plane indices in increasing axis order.
+__host__ __device__ __forceinline__ void plane_dims(const Geo& g, int axis, int* na, int* nb) {
+  *na = axis == 0 ? g.ny : g.nx;
+  *nb = g.dim == 2 ? 1 : (axis == 2 ? g.ny : g.nz);
+}
+
+__host__ __device__ __forceinline__ int64_t plane_node(const Geo& g, int axis, int idx, int64_t t) {
+  int na, nb;
+  plane_dims(g, axis, &na, &nb);
+  const int64_t np = (int64_t)na * nb;
+  const int q = (int)(t / np);
+  const int64_t p = t % np;
+  const int a = (int)(p % na), b = (int)(p / na);
+  int i, j, k;
+  if (g.dim == 2) {
+    k = 0;
+    if (axis == 0) { i = idx; j = a; } else { i = a; j = idx; }
+  } else if (axis == 0) { i = idx; j = a; k = b; }
+  else if (axis == 1) { i = a; j = idx; k = b; }
+  else { i = a; j = b; k = idx; }
+  return (int64_t)(g.nh + q) * g.ncell + ((int64_t)k * g.ny + j) * g.nx + i;
+}
+
+// Restart in Krylov dimension: polynomial degree + 1 of the interpolated
+// source on one sample interval, and the layout (in doubles) of the per-
+// restart set-up record: E = exp(-d H_m) (MMAX x MMAX, row-major), the
+// interval responses W_j (RST_P x MMAX), the last rows of H_m and H_m^2, and
+// the scalars h_{m+1,m}, (H_m)_{m,1}, m.
+constexpr int RST_P = 6;
+constexpr int RST_OFF_W = MMAX * MMAX;
+constexpr int RST_OFF_R1 = RST_OFF_W + RST_P * MMAX;
+constexpr int RST_OFF_R2 = RST_OFF_R1 + MMAX;
+constexpr int RST_OFF_SC = RST_OFF_R2 + MMAX;
+constexpr int RST_MATS = RST_OFF_SC + 8;
+
 struct Material {
   const void* inv_eps;   // (ncomp - nh) x ncell, 1 / mean eps on E nodes
   const void* sig2;      // sigma at 2*index + half along the layer axis
@@ -139,6 +177,19 @@ struct kx_ctx {
   int adj_nq_max = 0;
   void* d_zre;              // stationary parts, max_freqs x n (real)
   void* d_zim;              // stationary parts, max_freqs x n (imaginary)
+  // restart in Krylov dimension (rst_samples > 0)
+  double* d_rst_b = nullptr;     // 2 x max_freqs x rst_samples x RST_P source coefficients
+  double* d_rst_smp = nullptr;   // max_freqs x (rst_samples + 1) x 3 alphahat samples
+  double* d_rst_mats = nullptr;  // set-up record of the current restart
+  double* d_rst_u = nullptr;     // MAXF x MMAX projected solutions u(T)
+  double* d_rst_res = nullptr;   // MAXF residual maxima
+  int* d_rst_state = nullptr;    // MAXF: 0 active, 1 stops after this restart, 2 stopped
+  double* d_rst_yp = nullptr;    // max_freqs x plane-node accumulators
+  int64_t rst_plane_max = 0;     // plane nodes the accumulators hold per frequency
+  cudaStream_t aux_stream = nullptr;   // projected work overlapping the next Arnoldi process
+  int side_ctas = 0;        // long-lived CTAs of other kernels sharing the SMs meanwhile
+  cudaEvent_t ev_arnoldi = nullptr;    // Arnoldi process of a restart complete
+  cudaEvent_t ev_proj[2] = {nullptr, nullptr};  // projected work done with basis slot 0 / 1
   kx_stats stats;
   char err[512] = {0};   // fixed buffer: recording an error allocates nothing
   // per-kernel-class timing (kx_set_timing)
@@ -180,6 +231,21 @@ kx_status launch_response(kx_ctx* c, int f, const double* h_om, double T, int sp
                           const void* zre, const void* zim, const void* Y, int plane_axis,
                           int plane_idx, void* E_plane, double* d_intensity, void* Yout);
 
+// rstdim.cu
+// (launches on stream st: the context's stream, or its auxiliary stream
+// when the projected work overlaps the next restart's Arnoldi process)
+kx_status launch_rst_source(kx_ctx* c, cudaStream_t st, int nfreq, double beta, int Nt, double d, double* b);
+kx_status launch_rst_setup(kx_ctx* c, cudaStream_t st, int slot, double d);
+kx_status launch_rst_cascade(kx_ctx* c, cudaStream_t st, int nfreq, const double* b, int Nt, double d,
+                             double tol_abs);
+kx_status launch_rst_coef(kx_ctx* c, cudaStream_t st, int nfreq, double* b, int Nt, double d);
+kx_status launch_rst_plane(kx_ctx* c, cudaStream_t st, int slot, int nfreq, int axis, int idx, int64_t P);
+kx_status launch_rst_full(kx_ctx* c, cudaStream_t st, int slot, int nfreq, void* Y);
+kx_status launch_rst_out(kx_ctx* c, cudaStream_t st, int nfreq, int64_t P, void* E_plane, double* d_intensity,
+                         void* Y);
+// column m_done of basis slot `from` (the unnormalised v_{m+1}) -> column 0 of slot `to`
+kx_status launch_rst_nextvec(kx_ctx* c, cudaStream_t st, int from, int to);
+
 // projected.cu
 kx_status launch_substep_control(kx_ctx* c, int slot0, int ns);
 kx_status launch_expm_project(kx_ctx* c, const double* dH, int ldh, int m, double beta,
@@ -191,6 +257,14 @@ size_t expm_smem_bytes(int msz);
 // Persistent grid for a kernel: resident blocks (occupancy) x SMs, capped
 // by the work and by the partial-sum stride.
 int persistent_grid(kx_ctx* c, const void* kernel, int64_t items_per_block_round, size_t smem);
+
+// A persistent grid of gr blocks (full occupancy) shrunk by the CTAs that
+// other, concurrently running kernels keep resident, so that every block
+// still finds a slot in the first wave.
+inline int reserve_grid(const kx_ctx* c, int nb, int gr) {
+  if (c->side_ctas <= 0) return nb;
+  return std::min(nb, std::max(c->nsm, gr - c->side_ctas));
+}
 
 // Timing brackets around one launch (no-ops unless timing is on).
 void time_begin(kx_ctx* c);

@@ -145,7 +145,8 @@ kx_status launch_pass_b(kx_ctx* c, int slot, int ns, int j) {
     grid[fp64] = persistent_grid(c, fp64 ? (const void*)k_pass_b<double> : (const void*)k_pass_b<float>,
                                  1 << 30, 0);
   const int64_t rounds = (c->n / (fp64 ? 2 : 4) + NTHREADS - 1) / NTHREADS;
-  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(rounds, grid[fp64].load()), c->ps));
+  const int nb = reserve_grid(c, (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(rounds, grid[fp64].load()), c->ps)),
+                             grid[fp64].load());
   if (fp64) {
     k_pass_b<double><<<dim3(nb, ns), NTHREADS, 0, c->stream>>>(make_slotset<double>(c, slot), j, c->n, c->ld,
                                                               ldh, aug, 1e-12);
@@ -476,27 +477,11 @@ __global__ void k_plane(Geo g, int split, double sW, double cW, const T* __restr
                         T* __restrict__ E_plane, double* intensity) {
   const int nE = g.ncomp - g.nh;
   int na, nb;
-  if (g.dim == 2) {
-    na = axis == 0 ? g.ny : g.nx;
-    nb = 1;
-  } else {
-    na = axis == 0 ? g.ny : g.nx;
-    nb = axis == 2 ? g.ny : g.nz;
-  }
+  plane_dims(g, axis, &na, &nb);
   const int64_t np = (int64_t)na * nb;
   double acc = 0.0;
   for (int64_t t = threadIdx.x; t < nE * np; t += blockDim.x) {
-    const int q = (int)(t / np);
-    const int64_t p = t % np;
-    const int a = (int)(p % na), b = (int)(p / na);
-    int i, j, k;
-    if (g.dim == 2) {
-      k = 0;
-      if (axis == 0) { i = idx; j = a; } else { i = a; j = idx; }
-    } else if (axis == 0) { i = idx; j = a; k = b; }
-    else if (axis == 1) { i = a; j = idx; k = b; }
-    else { i = a; j = b; k = idx; }
-    const int64_t e = (int64_t)(g.nh + q) * g.ncell + ((int64_t)k * g.ny + j) * g.nx + i;
+    const int64_t e = plane_node(g, axis, idx, t);
     double val = (double)yt[e];
     if (split) val = sW * (double)zr[e] + cW * (double)zi[e] - val;
     if (E_plane) E_plane[t] = (T)val;

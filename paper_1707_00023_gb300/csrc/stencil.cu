@@ -433,7 +433,7 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int ns, int j, const void* gaug) 
     else fn = gaug ? (const void*)k_pass_a<T, 3, 1, TableMat<T>> : (const void*)k_pass_a<T, 3, 0, TableMat<T>>;
     gr = persistent_grid(c, fn, 1 << 30, 0);
   }
-  const int nb = (int)std::min<int64_t>(std::min<int64_t>(rounds, gr.load()), c->ps);
+  const int nb = reserve_grid(c, (int)std::min<int64_t>(std::min<int64_t>(rounds, gr.load()), c->ps), gr.load());
   const dim3 grd(nb, ns);
   if (vec4) {
     SlotSet<float> sf = make_slotset<float>(c, slot);

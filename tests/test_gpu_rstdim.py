@@ -1,0 +1,235 @@
+"""GPU parity of restart in Krylov dimension (Sect. 3.4, eq. (rst),
+Corollary 2, Fig. alg:rst) through the C ABI.
+
+Against the oracle (exact realisations of alphahat, no time sampling) at a
+fixed number of restarts, which checks the restart mechanics themselves,
+and against the exact solution once converged.  Tolerances: the GPU
+replaces each alphahat by its quintic Hermite interpolant on the sample
+grid (relative error about 1e-12 at the FP64 spacing, 1e-9 at the FP32 one);
+intermediate restarts amplify every rounding by the growth of alphahat (a
+few times on these cases), so FP64 is held to 1e-9 relative L2 and FP32 to
+3e-6 (three times the response accuracy target).
+"""
+import numpy as np
+import pytest
+
+import scenario as S
+from oracle import exact, restart, yee
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+from paper_1707_00023_gb300 import Context, KxError  # noqa: E402
+from paper_1707_00023_gb300._binding import KX_EINVAL, KX_ENOCONV  # noqa: E402
+
+TOL = {"fp64": 1e-9, "fp32": 3e-6}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(x, prec):
+    return torch.tensor(np.asarray(x), dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda")
+
+
+CASES = {
+    # ragged sizes; a random source so that several restarts are needed
+    "2d": (S.Grid(2, (37, 29), (S.PEC, S.PEC), 0, 4, 1.0), 16, 25.0),
+    "3d": (S.Grid(3, (14, 11, 13), (S.PERIODIC, S.PERIODIC, S.PEC), 2, 2, 1.0), 24, 20.0),
+}
+
+
+def make(name):
+    grid, m, T = CASES[name]
+    eps = 1.0 + 3.0 * np.random.default_rng(11).random(grid.shape)
+    g = S.masked_random_vector(grid, 12)
+    la = grid.layer_axis
+    plane = (la, grid.n[la] - grid.layer_cells - 2)
+    return grid, eps, g, m, T, plane
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fixed_restarts_match_oracle(name, prec):
+    grid, eps, g, m, T, plane = make(name)
+    op = yee.Operator(grid, eps)
+    oms = [0.9, 1.1]
+    K = 3
+    ctx = Context(grid, eps, precision=prec, krylov_dim=m, max_freqs=2, rst_samples=20000)
+    out = ctx.response_restart_dim(dev(g, prec), oms, T, rtol=0.0, max_restarts=K, plane=plane,
+                                   want_full=True, allow_noconv=True)
+    assert out["status"] == KX_ENOCONV
+    assert list(out["restarts"]) == [K, K]
+    ref = restart.restart_dim(op.apply, g, oms, T, m, max_restarts=K, rtol=0.0)
+    for f in range(2):
+        y = ref["y"][f]
+        Pw = yee.plane_fields(grid, y, plane)
+        assert rel(out["Y"][f].double().cpu().numpy(), y) < TOL[prec]
+        assert rel(out["E_plane"][f].double().cpu().numpy(), Pw) < TOL[prec]
+        assert abs(out["intensity"][f] - (Pw * Pw).sum()) < 2 * TOL[prec] * (Pw * Pw).sum()
+        # the residual the GPU reports is the oracle's (sampled on other grids)
+        assert abs(out["resid"][f] * np.linalg.norm(g) - ref["resid"][f]) < 0.05 * ref["resid"][f]
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_converged_matches_exact(prec):
+    grid, eps, g, m, T, plane = make("3d")
+    A = yee.Operator(grid, eps).matrix()
+    oms = S.freq_list(3)
+    rtol = 1e-11 if prec == "fp64" else 1e-7
+    ctx = Context(grid, eps, precision=prec, krylov_dim=m, max_freqs=3, rst_samples=20000)
+    out = ctx.response_restart_dim(dev(g, prec), oms, T, rtol=rtol, plane=plane, want_full=True)
+    assert np.all(out["restarts"] >= 3)
+    assert np.all(out["resid"] <= rtol)
+    for f, W in enumerate(oms):
+        want = exact.y_plain(A, g, W, T)
+        assert rel(out["Y"][f].double().cpu().numpy(), want) < TOL[prec]
+        # plane values against the field's norm: the plane carries a small
+        # share of it, and FP32 rounding is spread over the whole field
+        Pw = yee.plane_fields(grid, want, plane)
+        dP = np.linalg.norm(out["E_plane"][f].double().cpu().numpy() - Pw)
+        assert dP < TOL[prec] * (np.linalg.norm(Pw) if prec == "fp64" else np.linalg.norm(want))
+    ctx.close()
+
+
+def test_frequencies_are_independent_and_deterministic():
+    """Corollary 2 on the GPU: a frequency's response does not depend on
+    which other frequencies share the bases (bitwise), and repeated calls
+    give the same bits."""
+    grid, eps, g, m, T, plane = make("2d")
+    ctx = Context(grid, eps, precision="fp32", krylov_dim=m, max_freqs=3, rst_samples=20000)
+    gd = dev(g, "fp32")
+    joint = ctx.response_restart_dim(gd, [0.8, 1.0, 1.2], T, rtol=1e-7, plane=plane)
+    again = ctx.response_restart_dim(gd, [0.8, 1.0, 1.2], T, rtol=1e-7, plane=plane)
+    assert torch.equal(joint["E_plane"], again["E_plane"])
+    for f, W in enumerate([0.8, 1.0, 1.2]):
+        alone = ctx.response_restart_dim(gd, [W], T, rtol=1e-7, plane=plane)
+        assert torch.equal(alone["E_plane"][0], joint["E_plane"][f])
+        assert alone["restarts"][0] == joint["restarts"][f]
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_overlapped_restarts_equal_sequential(prec):
+    """With two basis slots the projected work of restart k runs on an
+    auxiliary stream beside restart k+1's Arnoldi process; the arithmetic is
+    the same, so the bits are too (one slot, and per-kernel timing, run
+    everything on the context stream)."""
+    grid, eps, g, m, T, plane = make("3d")
+    oms = [0.85, 1.0, 1.15]
+    outs = []
+    for batch, timing in ((1, False), (2, False), (2, True)):
+        ctx = Context(grid, eps, precision=prec, krylov_dim=m, max_freqs=3, batch=batch, rst_samples=20000)
+        ctx.set_timing(timing)
+        outs.append(ctx.response_restart_dim(dev(g, prec), oms, T, rtol=1e-7, plane=plane, want_full=True))
+        if timing:
+            kt = ctx.kernel_times()
+            assert kt["cascade"]["launches"] >= 3 and kt["cascade"]["ms"] > 0.0
+        ctx.close()
+    for o in outs[1:]:
+        assert torch.equal(o["E_plane"], outs[0]["E_plane"]) and torch.equal(o["Y"], outs[0]["Y"])
+        np.testing.assert_array_equal(o["restarts"], outs[0]["restarts"])
+
+
+def test_method_dispatch_equals_entry_point():
+    grid, eps, g, m, T, plane = make("2d")
+    ctx = Context(grid, eps, precision="fp64", krylov_dim=m, max_freqs=2, rst_samples=20000)
+    gd = dev(g, "fp64")
+    a = ctx.response_at_freqs(gd, [0.9, 1.1], T, rtol=1e-10, method="rstdim", plane=plane, want_full=True)
+    b = ctx.response_restart_dim(gd, [0.9, 1.1], T, rtol=1e-10, plane=plane, want_full=True)
+    assert torch.equal(a["Y"], b["Y"]) and torch.equal(a["E_plane"], b["E_plane"])
+    np.testing.assert_array_equal(a["err_est"], b["resid"])
+    ctx.close()
+
+
+def test_zero_source():
+    grid, eps, g, m, T, plane = make("2d")
+    ctx = Context(grid, eps, precision="fp32", krylov_dim=m, max_freqs=2, rst_samples=2000)
+    out = ctx.response_restart_dim(torch.zeros(grid.nunk, dtype=torch.float32, device="cuda"), [1.0, 1.1], T,
+                                   plane=plane, want_full=True)
+    assert float(out["Y"].abs().max()) == 0.0 and float(out["E_plane"].abs().max()) == 0.0
+    assert np.all(out["intensity"] == 0.0) and np.all(out["restarts"] == 0)
+    ctx.close()
+
+
+def test_invariant_subspace_is_exact_in_one_restart():
+    """m above the dimension of the Krylov space: the Arnoldi process breaks
+    down, alphahat = 0 and one restart gives the exact response."""
+    grid = S.Grid(2, (4, 3), (S.PEC, S.PEC), 0, 1, 0.5)
+    eps = 1.0 + np.random.default_rng(3).random(grid.shape)
+    g = S.masked_random_vector(grid, 5)
+    A = yee.Operator(grid, eps).matrix()
+    ctx = Context(grid, eps, precision="fp64", krylov_dim=64, max_freqs=1, rst_samples=4000)
+    out = ctx.response_restart_dim(dev(g, "fp64"), [1.0], 7.0, rtol=1e-12, plane=(0, 2), want_full=True)
+    # CGS flags the breakdown relative to max ||A v_j|| (1e-12 in FP64)
+    assert out["restarts"][0] == 1 and out["resid"][0] <= 1e-12
+    assert rel(out["Y"][0].cpu().numpy(), exact.y_plain(A, g, 1.0, 7.0)) < 1e-10
+    ctx.close()
+
+
+def test_invalid_arguments_are_rejected():
+    grid, eps, g, m, T, plane = make("2d")
+    gd = dev(g, "fp32")
+    ctx = Context(grid, eps, precision="fp32", krylov_dim=m, max_freqs=2)
+    with pytest.raises(KxError, match="rst_samples = 0"):
+        ctx.response_restart_dim(gd, [1.0], T, plane=plane)
+    ctx.close()
+    ctx = Context(grid, eps, precision="fp32", krylov_dim=m, max_freqs=2, rst_samples=1000)
+    with pytest.raises(KxError, match="250000 time samples") as e:
+        ctx.response_restart_dim(gd, [1.0], T, dt_sample=1e-4, plane=plane)
+    assert e.value.status == KX_EINVAL
+    for kw in ({"dt_sample": -1.0}, {"max_restarts": -1}, {"rtol": -1e-3}, {"rtol": float("nan")}):
+        with pytest.raises(KxError):
+            ctx.response_restart_dim(gd, [1.0], T, plane=plane, **kw)
+    with pytest.raises(KxError):
+        ctx.response_restart_dim(gd, [1.0], -1.0, plane=plane)
+    with pytest.raises(KxError):
+        ctx.response_restart_dim(gd, [1.0], T, plane=(2, 0))
+    with pytest.raises(KxError):
+        ctx.response_restart_dim(gd, [1.0, 1.1, 1.2], T, plane=plane)   # more than max_freqs
+    # the context stays usable
+    out = ctx.response_restart_dim(gd, [1.0], T, rtol=1e-7, plane=plane)
+    assert out["status"] == 0
+    ctx.close()
+
+
+def test_multi_problem_driver_with_restart_in_dimension():
+    from paper_1707_00023_gb300 import response_multi
+    scs = S.config_uneven(count=3, seed=6, nmin=8, nmax=12, T=15.0, m=24, nfreq=2)
+    ctxs, gs = [], []
+    for sc in scs:
+        ctxs.append(Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=24, max_freqs=2,
+                            stream="own", rst_samples=4000))
+        gs.append(dev(sc.g, "fp64"))
+    torch.cuda.synchronize()
+    oms = np.stack([sc.omegas for sc in scs])
+    planes = np.array([sc.plane for sc in scs])
+    inten, _ = response_multi(ctxs, gs, oms, 15.0, rtol=1e-11, method="rstdim", planes=planes, nthreads=3)
+    for i, sc in enumerate(scs):
+        A = yee.Operator(sc.grid, sc.eps_cell).matrix()
+        want = yee.intensity(sc.grid, exact.y_plain(A, sc.g, sc.omegas[0], 15.0), sc.plane)
+        assert abs(inten[i, 0] - want) < 1e-9 * want
+    for c in ctxs:
+        c.close()
+
+
+def test_full_size_3d64_T400_against_time_restarted_fp64():
+    """The benchmark's configuration (3D 64^3, m = 64, T = 400, 32
+    frequencies) by restart in dimension in FP32, against the FP64
+    time-restarted method (an independent algorithm, itself oracle-checked)
+    on the first and last frequency: plane fields within 3e-6."""
+    sc = S.config_3d(n=64, seed=1709, fill=0.3, T=400.0, m=64)
+    oms = S.freq_list(32)
+    ctx = Context(sc.grid, sc.eps_cell, precision="fp32", krylov_dim=64, max_freqs=32, rst_samples=4096)
+    a = ctx.response_restart_dim(dev(sc.g, "fp32"), oms, sc.T, rtol=1e-7, plane=sc.plane)
+    ctx.close()
+    assert np.all(a["resid"] <= 1e-7)
+    ctx = Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=64, max_freqs=2, batch=2)
+    b = ctx.response_at_freqs(dev(sc.g, "fp64"), oms[[0, 31]], sc.T, rtol=1e-11, method="plain", plane=sc.plane)
+    ctx.close()
+    for k, f in enumerate((0, 31)):
+        assert rel(a["E_plane"][f].double().cpu().numpy(), b["E_plane"][k].cpu().numpy()) < 3e-6
