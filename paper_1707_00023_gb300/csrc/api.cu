@@ -747,9 +747,14 @@ kx_status response_restart_dim(kx_ctx* c, const void* d_g, const double* omegas,
   // modes: the grid fixes the order of the reductions, so the bits agree)
   struct SideCtas {
     kx_ctx* c;
-    ~SideCtas() { c->side_ctas = 0; }
+    ~SideCtas() {
+      c->side_ctas = 0;
+      c->pdl = 0;
+    }
   } side{c};
   c->side_ctas = nfreq + 1;
+  // the Arnoldi chain of this method runs with programmatic dependent launch
+  c->pdl = 1;
   const size_t vbytes = (size_t)c->n * c->esize;
   // restart 1 starts from v_1 = g / ||g|| in slot 0
   KX_CUDA(c, cudaMemcpyAsync(slot_col(c, 0, 0), d_g, vbytes, cudaMemcpyDeviceToDevice, A), "copy g");

@@ -188,6 +188,7 @@ struct kx_ctx {
   int64_t rst_plane_max = 0;     // plane nodes the accumulators hold per frequency
   cudaStream_t aux_stream = nullptr;   // projected work overlapping the next Arnoldi process
   int side_ctas = 0;        // long-lived CTAs of other kernels sharing the SMs meanwhile
+  int pdl = 0;              // launch the Arnoldi chain with programmatic dependent launch
   cudaEvent_t ev_arnoldi = nullptr;    // Arnoldi process of a restart complete
   cudaEvent_t ev_proj[2] = {nullptr, nullptr};  // projected work done with basis slot 0 / 1
   kx_stats stats;
@@ -257,6 +258,37 @@ size_t expm_smem_bytes(int msz);
 // Persistent grid for a kernel: resident blocks (occupancy) x SMs, capped
 // by the work and by the partial-sum stride.
 int persistent_grid(kx_ctx* c, const void* kernel, int64_t items_per_block_round, size_t smem);
+
+// Programmatic dependent launch.  A kernel of the Arnoldi chain may be
+// launched while its predecessor in the stream is still running; it waits
+// (griddepcontrol.wait: the predecessor grid has completed and its memory
+// is visible) before touching any data, and lets its own successor start
+// launching right away.  Without a programmatic predecessor the wait
+// returns at once.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(const kx_ctx* c, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t st, Args... args) {
+  if (c->pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+  } else {
+    kern<<<grid, block, smem, st>>>(args...);
+  }
+}
 
 // A persistent grid of gr blocks (full occupancy) shrunk by the CTAs that
 // other, concurrently running kernels keep resident, so that every block

@@ -44,6 +44,7 @@ template <> __device__ __forceinline__ double2 vzero<double>() { return make_dou
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS) k_pass_b(SlotSet<T> ss, int j, int64_t n, int64_t ld,
                                                     int ldh, int aug, double btol) {
+  pdl_enter();
   using V4 = typename Vec<T>::t;
   constexpr int W = Vec<T>::w;
   const Slot<T> s = slot_at(ss, blockIdx.y);
@@ -91,28 +92,45 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_b(SlotSet<T> ss, int j, int64
 }
 
 // Finalisation of pass B (one block): h_{j+1,j} = ||w||, scale, breakdown.
+// The augmented entries of w (plain method only) get the same Gram-Schmidt
+// update, their column sums spread over the block and reduced in a fixed
+// order; slots without augmented entries skip it (the entries are zero).
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS) k_fin_b(SlotSet<T> ss, int j, int ldh, int nb, int aug, double btol) {
+  pdl_enter();
   const Slot<T> s = slot_at(ss, blockIdx.y);
   if (s.st->done || s.st->retired) return;
   const int ncol = j + 1;
-  double x = 0.0;
+  const bool augm = aug && s.st->aug;
+  double x = 0.0, pa = 0.0, pb = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) x += __ldcg(s.part + b);
-  __shared__ double red[NWARPS];
+  if (augm) {
+    for (int col = threadIdx.x; col < ncol; col += blockDim.x) {
+      const double cc = s.H[col + (int64_t)j * ldh] * s.scale[col];
+      pa += cc * s.aug[2 * col];
+      pb += cc * s.aug[2 * col + 1];
+    }
+  }
+  __shared__ double red[3][NWARPS];
   x = warp_sum(x);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  pa = warp_sum(pa);
+  pb = warp_sum(pb);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = x;
+    red[1][threadIdx.x >> 5] = pa;
+    red[2][threadIdx.x >> 5] = pb;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tot = 0.0;
+    double tot = 0.0, sa = 0.0, sb = 0.0;
 #pragma unroll
-    for (int w = 0; w < NWARPS; ++w) tot += red[w];
-    if (aug) {
-      double a = s.aug[2 * (j + 1)], b = s.aug[2 * (j + 1) + 1];
-      for (int col = 0; col < ncol; ++col) {
-        const double cc = s.H[col + (int64_t)j * ldh] * s.scale[col];
-        a -= cc * s.aug[2 * col];
-        b -= cc * s.aug[2 * col + 1];
-      }
+    for (int w = 0; w < NWARPS; ++w) {
+      tot += red[0][w];
+      sa += red[1][w];
+      sb += red[2][w];
+    }
+    if (augm) {
+      const double a = s.aug[2 * (j + 1)] - sa, b = s.aug[2 * (j + 1) + 1] - sb;
       s.aug[2 * (j + 1)] = a;
       s.aug[2 * (j + 1) + 1] = b;
       tot += a * a + b * b;
@@ -148,15 +166,17 @@ kx_status launch_pass_b(kx_ctx* c, int slot, int ns, int j) {
   const int nb = reserve_grid(c, (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(rounds, grid[fp64].load()), c->ps)),
                              grid[fp64].load());
   if (fp64) {
-    k_pass_b<double><<<dim3(nb, ns), NTHREADS, 0, c->stream>>>(make_slotset<double>(c, slot), j, c->n, c->ld,
-                                                              ldh, aug, 1e-12);
+    launch_k(c, k_pass_b<double>, dim3(nb, ns), NTHREADS, 0, c->stream, make_slotset<double>(c, slot), j, c->n,
+             c->ld, ldh, aug, 1e-12);
     KX_CHECK_LAUNCH(c);
-    k_fin_b<double><<<dim3(1, ns), NTHREADS, 0, c->stream>>>(make_slotset<double>(c, slot), j, ldh, nb, aug, 1e-12);
+    launch_k(c, k_fin_b<double>, dim3(1, ns), NTHREADS, 0, c->stream, make_slotset<double>(c, slot), j, ldh, nb, aug,
+             1e-12);
   } else {
-    k_pass_b<float><<<dim3(nb, ns), NTHREADS, 0, c->stream>>>(make_slotset<float>(c, slot), j, c->n, c->ld,
-                                                             ldh, aug, 1e-6);
+    launch_k(c, k_pass_b<float>, dim3(nb, ns), NTHREADS, 0, c->stream, make_slotset<float>(c, slot), j, c->n, c->ld,
+             ldh, aug, 1e-6);
     KX_CHECK_LAUNCH(c);
-    k_fin_b<float><<<dim3(1, ns), NTHREADS, 0, c->stream>>>(make_slotset<float>(c, slot), j, ldh, nb, aug, 1e-6);
+    launch_k(c, k_fin_b<float>, dim3(1, ns), NTHREADS, 0, c->stream, make_slotset<float>(c, slot), j, ldh, nb, aug,
+             1e-6);
   }
   KX_CHECK_LAUNCH(c);
   return KX_OK;
@@ -183,6 +203,7 @@ __device__ __forceinline__ void acc_comp(float& s, float& c, float hi, float lo,
 
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS) k_restart(SlotSet<T> ss, int64_t n, int64_t ld, int mode) {
+  pdl_enter();
   using V4 = typename Vec<T>::t;
   constexpr int W = Vec<T>::w;
   const Slot<T> s = slot_at(ss, blockIdx.y);
@@ -307,7 +328,7 @@ template <typename T>
 static kx_status restart_t(kx_ctx* c, int slot, int ns, int mode) {
   // bytes: combine reads the m basis columns and writes one; norm reads one
   time_begin(c);
-  k_restart<T><<<dim3(c->nblk, ns), NTHREADS, 0, c->stream>>>(make_slotset<T>(c, slot), c->n, c->ld, mode);
+  launch_k(c, k_restart<T>, dim3(c->nblk, ns), NTHREADS, 0, c->stream, make_slotset<T>(c, slot), c->n, c->ld, mode);
   time_end(c, KX_K_RESTART, (mode == 1 ? c->m + 1.0 : 1.0) * c->n * c->esize * ns);
   KX_CHECK_LAUNCH(c);
   return KX_OK;

@@ -129,6 +129,7 @@ kx_status launch_apply(kx_ctx* c, const void* v, void* w, int transpose) {
 template <typename T, int DIM, int AUG, typename Mat, int TR = 0>
 __global__ void __launch_bounds__(NTHREADS) k_pass_a(Geo g, SlotSet<T> ss, int j, int64_t ld, Mat mat,
                                                     const T* __restrict__ gsrc) {
+  pdl_enter();
   constexpr int NC = DIM == 2 ? 3 : 6;
   const Slot<T> s = slot_at(ss, blockIdx.y);
   if (s.st->done || s.st->retired) return;
@@ -229,6 +230,7 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_a4(Geo g, SlotSet<float> ss, 
                                                      const float* __restrict__ ie,
                                                      const float* __restrict__ sig2,
                                                      const float* __restrict__ gsrc) {
+  pdl_enter();
   const Slot<float> s = slot_at(ss, blockIdx.y);
   if (s.st->done || s.st->retired) return;
   __shared__ double acc[NWARPS][MMAX + 2];
@@ -365,6 +367,7 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_a4(Geo g, SlotSet<float> ss, 
 // H[c, j] = scale[c] * d_c (plus the augmented entries' share), column j+1
 // gives ||w|| (breakdown scale) and the augmented entries of w.
 __global__ void __launch_bounds__(NTHREADS) k_fin_a(SlotSet<float> ss, int j, int ldh, int nb, int aug) {
+  pdl_enter();
   const Slot<float> sl = slot_at(ss, blockIdx.y);
   double* part = sl.part;
   const int ps = sl.ps;
@@ -439,18 +442,18 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int ns, int j, const void* gaug) 
     SlotSet<float> sf = make_slotset<float>(c, slot);
     const float* ief = (const float*)c->d_inv_eps;
     const float* sgf = (const float*)c->d_sig2;
-    if (gaug) k_pass_a4<1><<<grd, NTHREADS, 0, c->stream>>>(g, sf, j, c->ld, ief, sgf, (const float*)gaug);
-    else k_pass_a4<0><<<grd, NTHREADS, 0, c->stream>>>(g, sf, j, c->ld, ief, sgf, nullptr);
+    if (gaug) launch_k(c, k_pass_a4<1>, grd, NTHREADS, 0, c->stream, g, sf, j, c->ld, ief, sgf, (const float*)gaug);
+    else launch_k(c, k_pass_a4<0>, grd, NTHREADS, 0, c->stream, g, sf, j, c->ld, ief, sgf, (const float*)nullptr);
   } else if (g.dim == 2) {
-    if (gaug) k_pass_a<T, 2, 1, TableMat<T>><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
-    else k_pass_a<T, 2, 0, TableMat<T>><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
+    if (gaug) launch_k(c, k_pass_a<T, 2, 1, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
+    else launch_k(c, k_pass_a<T, 2, 0, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
   } else {
-    if (gaug) k_pass_a<T, 3, 1, TableMat<T>><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
-    else k_pass_a<T, 3, 0, TableMat<T>><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
+    if (gaug) launch_k(c, k_pass_a<T, 3, 1, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
+    else launch_k(c, k_pass_a<T, 3, 0, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
   }
   KX_CHECK_LAUNCH(c);
-  k_fin_a<<<dim3(j + 2, ns), NTHREADS, 0, c->stream>>>(make_slotset<float>(c, slot), j, ldh, nb,
-                                                       gaug != nullptr);
+  launch_k(c, k_fin_a, dim3(j + 2, ns), NTHREADS, 0, c->stream, make_slotset<float>(c, slot), j, ldh, nb,
+           (int)(gaug != nullptr));
   KX_CHECK_LAUNCH(c);
   return KX_OK;
 }
