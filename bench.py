@@ -2,9 +2,11 @@
 """Benchmark of the GB300 exponential-Krylov solver: frequency responses/s.
 
 One step = the whole hot path for one batch: the responses y_j(T) of eq.
-(ode) at the workload's frequencies (stationary parts from one shifted
-Krylov solve, transients by time-restarted exponential Krylov, output-plane
-extraction), on seeded synthetic random-scatterer media.
+(ode) at the workload's frequencies and their output-plane fields, on seeded
+synthetic random-scatterer media.  The default workload restarts in Krylov
+dimension with one basis per restart for all 32 frequencies (Fig. alg:rst);
+the other workloads run the time-restarted plain method (batched), the
+asymptotic splitting, the uneven multi-problem batch and the adjoint.
 
     python bench.py [--gpus N --steps K --warmup W] [--workload NAME] [--impl reference]
 
@@ -28,10 +30,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "freq responses/s at 1e-6 rel err vs per-freq Krylov; A·v+GS HBM GB/s"
 
-# DRAM bytes / algorithmic bytes per launch of the two hot kernels, from the
-# ncu capture summarised in profiles/arnoldi_passes_3d64_ncu.md (8-frequency
-# batch, step j = 50).  Set to None whenever those kernels change.
-NCU_TRAFFIC_RATIO = {"k_pass_a": 1.0015, "k_pass_b": 1.000}
+# DRAM bytes / algorithmic bytes per launch of the two Arnoldi kernels, from
+# the ncu captures summarised in profiles/rstdim_3d64_32f_ncu.md (single
+# basis, steps j = 60, 61).  Set to None whenever those kernels change.
+NCU_TRAFFIC_RATIO = {"k_pass_a": 1.012, "k_pass_b": 1.000}
 
 WORKLOADS = {
     # 3D Yee 64^3, random eps=2.25 spheres (fill 0.3, r 2-5), 8-cell layer,
@@ -50,6 +52,9 @@ WORKLOADS = {
     "3d64_m64_T400_32f_rst": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=32,
                                   prec="fp32", method="rstdim", rtol=1e-7, t_oracle=20.0, rst_samples=4096,
                                   batch=2),
+    "3d128_32f_T400_rst": dict(dim=3, n=128, seed=1710, fill=0.3, T=400.0, m=64, nfreq=32,
+                               prec="fp32", method="rstdim", rtol=1e-7, t_oracle=4.0, rst_samples=4096,
+                               batch=2),
     # 2D 64^2, 40 disks, FP64, m = 30, T = 200, plain method
     "2d64_m30_T200": dict(dim=2, n=64, seed=1708, T=200.0, m=30, nfreq=1, prec="fp64",
                           method="plain", rtol=1e-11, t_oracle=200.0),
@@ -63,7 +68,7 @@ WORKLOADS = {
     "adjoint3d96_8f": dict(kind="adjoint", dim=3, n=96, seed=1712, fill=0.3, T=400.0, m=64, nfreq=8,
                            prec="fp32", method="plain", rtol=1e-7, checkpoints=128),
 }
-DEFAULT = "3d64_m64_T400_32f"
+DEFAULT = "3d64_m64_T400_32f_rst"
 
 
 def shard_frequencies(nfreq, rank, world, lo=0.8, hi=1.2):
