@@ -90,7 +90,9 @@ SlotState fresh_state() {
 kx_status arnoldi_steps(kx_ctx* c, int slot0, int ns, int m, const void* g_aug) {
   for (int j = 0; j < m; ++j) {
     KX_TRY(launch_pass_a(c, slot0, ns, j, g_aug));
-    KX_TRY(launch_pass_b(c, slot0, ns, j));
+    // an augmented process finalises every pass B itself; otherwise the next
+    // pass A does, and only the last step needs the finalisation kernel
+    KX_TRY(launch_pass_b(c, slot0, ns, j, g_aug != nullptr || j == m - 1));
   }
   c->stats.arnoldi_steps += (int64_t)m * ns;
   c->stats.matvecs += (int64_t)m * ns;
@@ -984,11 +986,11 @@ kx_status adjoint_response_grad(kx_ctx* c, const void* d_g, const double* omegas
       KX_TRY(launch_norm_init(c, 0, 2));
       for (int j = 0; j < c->m; ++j) {
         KX_TRY(launch_pass_a(c, 0, 1, j, d_g));
-        KX_TRY(launch_pass_b(c, 0, 1, j));
+        KX_TRY(launch_pass_b(c, 0, 1, j, 1));
       }
       for (int j = 0; j < c->m; ++j) {
         KX_TRY(launch_pass_a_tr(c, 1, 1, j));
-        KX_TRY(launch_pass_b(c, 1, 1, j));
+        KX_TRY(launch_pass_b(c, 1, 1, j, j == c->m - 1));
       }
       c->stats.arnoldi_steps += 2 * (int64_t)c->m;
       c->stats.matvecs += 2 * (int64_t)c->m;

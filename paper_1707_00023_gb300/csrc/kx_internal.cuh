@@ -14,6 +14,7 @@ namespace kx {
 
 constexpr int MMAX = 64;            // largest Krylov dimension
 constexpr int PCOLS = MMAX + 3;     // partial-sum columns per slot
+constexpr int FINB_COL = PCOLS - 1; // pass B's norm partials (pass A writes columns <= MMAX)
 constexpr int NTHREADS = 256;       // threads per block of the bulk kernels
 constexpr int NWARPS = NTHREADS / 32;
 constexpr int MAXF = 64;            // largest number of frequencies per call
@@ -212,7 +213,10 @@ kx_status launch_pass_a(kx_ctx* c, int slot0, int ns, int j, const void* g_aug);
 kx_status launch_pass_a_tr(kx_ctx* c, int slot0, int ns, int j);
 // pass A reading the per-cell permittivity directly (no 1/eps table)
 kx_status launch_pass_a_cells(kx_ctx* c, int slot, int j, const double* d_eps_cell);
-kx_status launch_pass_b(kx_ctx* c, int slot0, int ns, int j);
+// pass B of step j; finalize = 1 launches its finalisation kernel, otherwise
+// the next step's pass A finalises it (non-augmented processes only)
+kx_status launch_pass_b(kx_ctx* c, int slot0, int ns, int j, int finalize);
+int pass_b_grid(kx_ctx* c);
 
 // adjoint.cu
 kx_status launch_adj_seed(kx_ctx* c, const void* y, void* lam, int axis, int idx);

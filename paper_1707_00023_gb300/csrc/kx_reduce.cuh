@@ -48,6 +48,46 @@ __device__ __forceinline__ void block_partial(double x, double* part, int ps, in
   __syncthreads();
 }
 
+// Finalisation of step j-1's pass B at the start of step j's pass A
+// (non-augmented processes): every block sums the same nbb partials in the
+// same order, so all reach the same h_{j,j-1} and the same breakdown
+// decision; block 0 records them.  Returns false where the process stops
+// (lucky breakdown or a non-finite norm); *sj receives scale_j = 1/h.
+template <typename T>
+__device__ __forceinline__ bool fin_prev_b(const Slot<T>& s, int j, int ldh, int nbb, double btol, double* sj) {
+  double x = 0.0;
+  for (int b = threadIdx.x; b < nbb; b += blockDim.x) x += __ldcg(s.part + (int64_t)FINB_COL * s.ps + b);
+  __shared__ double red[NWARPS];
+  __shared__ double res;
+  __shared__ int stop;
+  x = warp_sum(x);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+#pragma unroll
+    for (int w = 0; w < NWARPS; ++w) tot += red[w];
+    const double h = sqrt(tot);
+    int stp = 0;
+    double scl = 0.0;
+    if (!isfinite(h)) stp = 2;
+    else if (h <= btol * s.st->wmax) stp = 1;   // invariant subspace: the projection is exact
+    else scl = 1.0 / h;
+    if (blockIdx.x == 0) {
+      s.H[j + (int64_t)(j - 1) * ldh] = h;
+      s.st->m_done = j;
+      s.scale[j] = scl;
+      if (stp == 2) s.st->status = KX_ENONFINITE;
+      if (stp) s.st->done = 1;
+    }
+    res = scl;
+    stop = stp;
+  }
+  __syncthreads();
+  *sj = res;
+  return stop == 0;
+}
+
 // In the last block: tot[c] = sum over blocks of part[c * ps + b], c < ncols.
 __device__ __forceinline__ void grid_columns(const double* part, int ps, int ncols, double* tot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

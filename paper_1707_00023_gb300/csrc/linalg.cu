@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_b(SlotSet<T> ss, int j, int64
     w[e] = x;
     nrm += (double)x * (double)x;
   }
-  block_partial(nrm, s.part, s.ps, 0);
+  block_partial(nrm, s.part, s.ps, FINB_COL);
 }
 
 // Finalisation of pass B (one block): h_{j+1,j} = ||w||, scale, breakdown.
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(NTHREADS) k_fin_b(SlotSet<T> ss, int j, int ld
   const int ncol = j + 1;
   const bool augm = aug && s.st->aug;
   double x = 0.0, pa = 0.0, pb = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) x += __ldcg(s.part + b);
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) x += __ldcg(s.part + (int64_t)FINB_COL * s.ps + b);
   if (augm) {
     for (int col = threadIdx.x; col < ncol; col += blockDim.x) {
       const double cc = s.H[col + (int64_t)j * ldh] * s.scale[col];
@@ -150,35 +150,44 @@ __global__ void __launch_bounds__(NTHREADS) k_fin_b(SlotSet<T> ss, int j, int ld
   }
 }
 
-// Algorithmic bytes of pass B at step j: read w and V_0..V_j (j+2 vectors),
-// write the updated column (1).
-kx_status launch_pass_b(kx_ctx* c, int slot, int ns, int j) {
-  const int ldh = c->m + 1;
-  const int aug = 1;  // augmented entries are zero when unused
-  time_begin(c);
-  struct End { kx_ctx* c; int j, ns; ~End() { time_end(c, KX_K_PASS_B, (j + 3.0) * c->n * c->esize * ns); } } end{c, j, ns};
+// Grid of pass B: a persistent grid (shrunk for resident side CTAs); the
+// next pass A needs it to finalise pass B itself.
+int pass_b_grid(kx_ctx* c) {
   static std::atomic<int> grid[2];
   const int fp64 = c->d.precision == KX_FP64;
   if (!grid[fp64])
     grid[fp64] = persistent_grid(c, fp64 ? (const void*)k_pass_b<double> : (const void*)k_pass_b<float>,
                                  1 << 30, 0);
   const int64_t rounds = (c->n / (fp64 ? 2 : 4) + NTHREADS - 1) / NTHREADS;
-  const int nb = reserve_grid(c, (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(rounds, grid[fp64].load()), c->ps)),
-                             grid[fp64].load());
+  return reserve_grid(c, (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(rounds, grid[fp64].load()), c->ps)),
+                      grid[fp64].load());
+}
+
+// Algorithmic bytes of pass B at step j: read w and V_0..V_j (j+2 vectors),
+// write the updated column (1).
+kx_status launch_pass_b(kx_ctx* c, int slot, int ns, int j, int finalize) {
+  const int ldh = c->m + 1;
+  const int aug = 1;  // augmented entries are zero when unused
+  time_begin(c);
+  struct End { kx_ctx* c; int j, ns; ~End() { time_end(c, KX_K_PASS_B, (j + 3.0) * c->n * c->esize * ns); } } end{c, j, ns};
+  const int fp64 = c->d.precision == KX_FP64;
+  const int nb = pass_b_grid(c);
   if (fp64) {
     launch_k(c, k_pass_b<double>, dim3(nb, ns), NTHREADS, 0, c->stream, make_slotset<double>(c, slot), j, c->n,
              c->ld, ldh, aug, 1e-12);
     KX_CHECK_LAUNCH(c);
-    launch_k(c, k_fin_b<double>, dim3(1, ns), NTHREADS, 0, c->stream, make_slotset<double>(c, slot), j, ldh, nb, aug,
-             1e-12);
+    if (finalize)
+      launch_k(c, k_fin_b<double>, dim3(1, ns), NTHREADS, 0, c->stream, make_slotset<double>(c, slot), j, ldh, nb,
+               aug, 1e-12);
   } else {
     launch_k(c, k_pass_b<float>, dim3(nb, ns), NTHREADS, 0, c->stream, make_slotset<float>(c, slot), j, c->n, c->ld,
              ldh, aug, 1e-6);
     KX_CHECK_LAUNCH(c);
-    launch_k(c, k_fin_b<float>, dim3(1, ns), NTHREADS, 0, c->stream, make_slotset<float>(c, slot), j, ldh, nb, aug,
-             1e-6);
+    if (finalize)
+      launch_k(c, k_fin_b<float>, dim3(1, ns), NTHREADS, 0, c->stream, make_slotset<float>(c, slot), j, ldh, nb,
+               aug, 1e-6);
   }
-  KX_CHECK_LAUNCH(c);
+  if (finalize) KX_CHECK_LAUNCH(c);
   return KX_OK;
 }
 

@@ -163,7 +163,7 @@ extern "C" kx_status kx_arnoldi_noalloc(const kx_desc* desc, const double* d_eps
   if ((st = launch_norm_init(&c, 0, 1)) != KX_OK) return err(st, c.err);
   for (int j = 0; j < m; ++j) {
     if ((st = launch_pass_a_cells(&c, 0, j, d_eps_cell)) != KX_OK) return err(st, c.err);
-    if ((st = launch_pass_b(&c, 0, 1, j)) != KX_OK) return err(st, c.err);
+    if ((st = launch_pass_b(&c, 0, 1, j, j == m - 1)) != KX_OK) return err(st, c.err);
   }
   // normalise the basis in place (the stored columns carry their scales)
   if ((st = launch_basis_export(&c, 0, d_V, m)) != KX_OK) return err(st, c.err);

@@ -128,7 +128,7 @@ kx_status launch_apply(kx_ctx* c, const void* v, void* w, int transpose) {
 // The last block forms H[i, j] = scale[i] * d_i.
 template <typename T, int DIM, int AUG, typename Mat, int TR = 0>
 __global__ void __launch_bounds__(NTHREADS) k_pass_a(Geo g, SlotSet<T> ss, int j, int64_t ld, Mat mat,
-                                                    const T* __restrict__ gsrc) {
+                                                    const T* __restrict__ gsrc, int ldh, int nbb, double btol) {
   pdl_enter();
   constexpr int NC = DIM == 2 ? 3 : 6;
   const Slot<T> s = slot_at(ss, blockIdx.y);
@@ -137,7 +137,13 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_a(Geo g, SlotSet<T> ss, int j
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int q = threadIdx.x; q < NWARPS * (MMAX + 2); q += blockDim.x) (&acc[0][0])[q] = 0.0;
   __syncthreads();
-  const double sj = s.scale[j];
+  // step j-1's pass B is finalised here when nbb > 0 (no separate kernel)
+  double sj;
+  if (nbb > 0) {
+    if (!fin_prev_b(s, j, ldh, nbb, btol, &sj)) return;
+  } else {
+    sj = s.scale[j];
+  }
   const T tsj = (T)sj;
   const T* __restrict__ vin = s.V + (int64_t)j * ld;
   T* __restrict__ wout = s.V + (int64_t)(j + 1) * ld;
@@ -229,7 +235,8 @@ template <int AUG>
 __global__ void __launch_bounds__(NTHREADS) k_pass_a4(Geo g, SlotSet<float> ss, int j, int64_t ld,
                                                      const float* __restrict__ ie,
                                                      const float* __restrict__ sig2,
-                                                     const float* __restrict__ gsrc) {
+                                                     const float* __restrict__ gsrc, int ldh, int nbb,
+                                                     double btol) {
   pdl_enter();
   const Slot<float> s = slot_at(ss, blockIdx.y);
   if (s.st->done || s.st->retired) return;
@@ -237,7 +244,12 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_a4(Geo g, SlotSet<float> ss, 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int q = threadIdx.x; q < NWARPS * (MMAX + 2); q += blockDim.x) (&acc[0][0])[q] = 0.0;
   __syncthreads();
-  const double sj = s.scale[j];
+  double sj;
+  if (nbb > 0) {
+    if (!fin_prev_b(s, j, ldh, nbb, btol, &sj)) return;
+  } else {
+    sj = s.scale[j];
+  }
   const float tsj = (float)sj;
   const float* __restrict__ v = s.V + (int64_t)j * ld;
   float* __restrict__ wout = s.V + (int64_t)(j + 1) * ld;
@@ -412,6 +424,10 @@ __global__ void __launch_bounds__(NTHREADS) k_fin_a(SlotSet<float> ss, int j, in
   }
 }
 
+// Lucky-breakdown threshold relative to max ||A v_i||, by vector precision.
+template <typename T>
+constexpr double btol_of() { return sizeof(T) == 8 ? 1e-12 : 1e-6; }
+
 template <typename T>
 static kx_status pass_a_t(kx_ctx* c, int slot, int ns, int j, const void* gaug) {
   const Geo& g = c->geo;
@@ -438,18 +454,21 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int ns, int j, const void* gaug) 
   }
   const int nb = reserve_grid(c, (int)std::min<int64_t>(std::min<int64_t>(rounds, gr.load()), c->ps), gr.load());
   const dim3 grd(nb, ns);
+  // a non-augmented process finalises step j-1's pass B here
+  const int nbb = (j >= 1 && !gaug) ? pass_b_grid(c) : 0;
+  const double bt = btol_of<T>();
   if (vec4) {
     SlotSet<float> sf = make_slotset<float>(c, slot);
     const float* ief = (const float*)c->d_inv_eps;
     const float* sgf = (const float*)c->d_sig2;
-    if (gaug) launch_k(c, k_pass_a4<1>, grd, NTHREADS, 0, c->stream, g, sf, j, c->ld, ief, sgf, (const float*)gaug);
-    else launch_k(c, k_pass_a4<0>, grd, NTHREADS, 0, c->stream, g, sf, j, c->ld, ief, sgf, (const float*)nullptr);
+    if (gaug) launch_k(c, k_pass_a4<1>, grd, NTHREADS, 0, c->stream, g, sf, j, c->ld, ief, sgf, (const float*)gaug, ldh, nbb, bt);
+    else launch_k(c, k_pass_a4<0>, grd, NTHREADS, 0, c->stream, g, sf, j, c->ld, ief, sgf, (const float*)nullptr, ldh, nbb, bt);
   } else if (g.dim == 2) {
-    if (gaug) launch_k(c, k_pass_a<T, 2, 1, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
-    else launch_k(c, k_pass_a<T, 2, 0, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
+    if (gaug) launch_k(c, k_pass_a<T, 2, 1, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs, ldh, nbb, bt);
+    else launch_k(c, k_pass_a<T, 2, 0, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs, ldh, nbb, bt);
   } else {
-    if (gaug) launch_k(c, k_pass_a<T, 3, 1, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
-    else launch_k(c, k_pass_a<T, 3, 0, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs);
+    if (gaug) launch_k(c, k_pass_a<T, 3, 1, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs, ldh, nbb, bt);
+    else launch_k(c, k_pass_a<T, 3, 0, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs, ldh, nbb, bt);
   }
   KX_CHECK_LAUNCH(c);
   launch_k(c, k_fin_a, dim3(j + 2, ns), NTHREADS, 0, c->stream, make_slotset<float>(c, slot), j, ldh, nb,
@@ -472,8 +491,13 @@ static kx_status pass_a_cells_t(kx_ctx* c, int slot, int j, const double* eps) {
     gr = persistent_grid(c, g.dim == 2 ? (const void*)k_pass_a<T, 2, 0, CellMat<T>>
                                        : (const void*)k_pass_a<T, 3, 0, CellMat<T>>, 1 << 30, 0);
   const int nb = (int)std::min<int64_t>(std::min<int64_t>(rounds, gr.load()), c->ps);
-  if (g.dim == 2) k_pass_a<T, 2, 0, CellMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr);
-  else k_pass_a<T, 3, 0, CellMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr);
+  const int nbb = j >= 1 ? pass_b_grid(c) : 0;
+  if (g.dim == 2)
+    k_pass_a<T, 2, 0, CellMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr, c->m + 1, nbb,
+                                                                  btol_of<T>());
+  else
+    k_pass_a<T, 3, 0, CellMat<T>><<<nb, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr, c->m + 1, nbb,
+                                                                  btol_of<T>());
   KX_CHECK_LAUNCH(c);
   k_fin_a<<<j + 2, NTHREADS, 0, c->stream>>>(make_slotset<float>(c, slot), j, c->m + 1, nb, 0);
   KX_CHECK_LAUNCH(c);
@@ -495,8 +519,13 @@ static kx_status pass_a_tr_t(kx_ctx* c, int slot, int ns, int j) {
                                        : (const void*)k_pass_a<T, 3, 0, TableMat<T>, 1>, 1 << 30, 0);
   const int nb = (int)std::min<int64_t>(std::min<int64_t>(rounds, gr.load()), c->ps);
   const dim3 grd(nb, ns);
-  if (g.dim == 2) k_pass_a<T, 2, 0, TableMat<T>, 1><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr);
-  else k_pass_a<T, 3, 0, TableMat<T>, 1><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr);
+  const int nbb = j >= 1 ? pass_b_grid(c) : 0;
+  if (g.dim == 2)
+    k_pass_a<T, 2, 0, TableMat<T>, 1><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr, c->m + 1, nbb,
+                                                                       btol_of<T>());
+  else
+    k_pass_a<T, 3, 0, TableMat<T>, 1><<<grd, NTHREADS, 0, c->stream>>>(g, s, j, c->ld, mat, nullptr, c->m + 1, nbb,
+                                                                       btol_of<T>());
   KX_CHECK_LAUNCH(c);
   k_fin_a<<<dim3(j + 2, ns), NTHREADS, 0, c->stream>>>(make_slotset<float>(c, slot), j, c->m + 1, nb, 0);
   KX_CHECK_LAUNCH(c);
