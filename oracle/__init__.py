@@ -22,6 +22,9 @@ arXiv:1707.00023 it follows):
 * ``restart``  -- residual-based restarting in Krylov dimension with one
                   basis per restart for every frequency (Sect. 3.4,
                   eq. (rst), Corollary 2, Fig. alg:rst).
+* ``periodic`` -- the two uses of the source's periodicity (Sect. 3.5):
+                  source splitting, eq. (split2), and the neighbouring-
+                  frequency difference, eq. (4diff) in Fig. alg:spl1.
 * ``adjoint``  -- gradient of the output-plane intensity with respect to
                   per-cell permittivity (no counterpart in the paper).
 
