@@ -51,7 +51,7 @@ typedef enum {
 
 enum { KX_PERIODIC = 0, KX_PEC = 1 };
 enum { KX_FP64 = 0, KX_FP32 = 1 };
-enum { KX_PLAIN = 0, KX_SPLIT = 1, KX_RSTDIM = 2 };
+enum { KX_PLAIN = 0, KX_SPLIT = 1, KX_RSTDIM = 2, KX_SPLIT2 = 3, KX_SPLIT4D = 4 };
 
 /* Problem descriptor.  Grid of n[0] x n[1] (x n[2]) unit cells; the
  * absorbing layer (conductivity ramping linearly from 0 to sigma_max over
@@ -181,6 +181,18 @@ kx_status expm_action(kx_ctx* ctx, const void* d_y0, double T, double rtol,
  *     expm_action (Fig. alg:spl1 steps 1-3 for each frequency).
  *   method KX_RSTDIM: response_restart_dim with dt_sample = 0 and
  *     max_restarts = 0; err_est receives its resid.
+ *   method KX_SPLIT2: source splitting (eq. (split2)): restart in time on
+ *     subintervals of one source period dT_j = 2 pi / omega_j.  w2, the
+ *     solution from zero over one period (and over the remainder
+ *     r = T - K dT_j when T is not a whole number of periods), is found
+ *     once per frequency by the plain method; then y <- exp(-dT_j A) y + w2
+ *     on every later period (homogeneous problems only).  err_est receives
+ *     the summed error estimates of all pieces.
+ *   method KX_SPLIT4D: as KX_SPLIT, but the transient of each frequency
+ *     after the first comes from the previous one's (eq. (4diff), Fig.
+ *     alg:spl1 steps 4-6): yhat_j(T) = yhat_{j-1}(T) + exp(-TA)(Im z_j -
+ *     Im z_{j-1}), the difference solved to the tolerance of Im z_j itself;
+ *     frequencies are taken in the given order (neighbours should be close).
  *   plane: host int[2] = {axis, index}: output plane perpendicular to axis.
  *   d_E_plane: device, nfreq x nE x (plane nodes) scalars (nE = 1 in 2D:
  *     Ez; 3 in 3D: Ex, Ey at the plane, Ez half a cell above), or NULL.

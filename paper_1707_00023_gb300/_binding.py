@@ -18,8 +18,9 @@ LIBPATH = os.path.join(HERE, "libkx.so")
 KX_OK, KX_EINVAL, KX_ENOMEM, KX_ECUDA, KX_ENONFINITE, KX_ENOCONV, KX_ETIMEOUT = range(7)
 KX_PERIODIC, KX_PEC = 0, 1
 KX_FP64, KX_FP32 = 0, 1
-KX_PLAIN, KX_SPLIT, KX_RSTDIM = 0, 1, 2
-METHODS = {"plain": KX_PLAIN, "split": KX_SPLIT, "rstdim": KX_RSTDIM}
+KX_PLAIN, KX_SPLIT, KX_RSTDIM, KX_SPLIT2, KX_SPLIT4D = 0, 1, 2, 3, 4
+METHODS = {"plain": KX_PLAIN, "split": KX_SPLIT, "rstdim": KX_RSTDIM, "split2": KX_SPLIT2,
+           "split4d": KX_SPLIT4D}
 STATUS_NAMES = {0: "KX_OK", 1: "KX_EINVAL", 2: "KX_ENOMEM", 3: "KX_ECUDA",
                 4: "KX_ENONFINITE", 5: "KX_ENOCONV", 6: "KX_ETIMEOUT"}
 

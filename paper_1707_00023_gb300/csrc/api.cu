@@ -284,6 +284,98 @@ kx_status stationary_core(kx_ctx* c, const void* d_g, const double* omegas, int 
   return KX_OK;
 }
 
+// One time loop over slots [0, ns): slot q (if on[q]) advances its column 0
+// over Tq[q] -- by the augmented plain method (source phase from zero) when
+// aug, else homogeneously; the other slots stay retired.  Error estimates are
+// added to err[q].
+kx_status slots_time_loop(kx_ctx* c, int ns, bool aug, const void* d_g, const double* omegas, int f0,
+                          double rtol, double eta, const std::vector<double>& Tq, const std::vector<char>& on,
+                          std::vector<double>& err) {
+  bool any = false;
+  for (int q = 0; q < ns; ++q) {
+    SlotState s = fresh_state();
+    if (!on[q]) {
+      s.retired = 1;
+    } else {
+      any = true;
+      s.T = Tq[q];
+      s.rtol = rtol;
+      if (aug) {
+        s.aug = 1;
+        s.omega = omegas[f0 + q];
+        s.eta = eta;
+        s.tol_mode = 1;
+      }
+    }
+    c->h_state[q] = s;
+  }
+  if (!any) return KX_OK;
+  KX_CUDA(c, cudaMemcpyAsync(c->d_state, c->h_state, sizeof(SlotState) * ns, cudaMemcpyHostToDevice, c->stream),
+          "state upload");
+  KX_TRY(sync(c));
+  std::vector<double> e(ns, 0.0);
+  KX_TRY(time_loop(c, 0, ns, aug ? d_g : nullptr, e.data()));
+  for (int q = 0; q < ns; ++q)
+    if (on[q]) err[q] += e[q];
+  return KX_OK;
+}
+
+// Source splitting (eq. (split2)) for frequencies f0 .. f0+ns-1 in slots
+// 0 .. ns-1, leaving y_f(T) in column 0 of slot q.  Subinterval dT = one
+// source period (the source has the same phase at every subinterval start,
+// so w2 is the same on all of them): w2(dT) is kept in d_zre[f], w2 over the
+// remainder r = T - K dT in d_zim[f].
+kx_status split2_wave(kx_ctx* c, const void* d_g, const double* omegas, int f0, int ns, double T, double rtol,
+                      double eta, double* err_est) {
+  const size_t vb = (size_t)c->n * c->esize;
+  const double two_pi = 6.283185307179586476925286766559;
+  std::vector<double> dT(ns), rem(ns), err(ns, 0.0);
+  std::vector<int> K(ns);
+  std::vector<char> all(ns, 1), has_r(ns, 0);
+  int Kmax = 0;
+  for (int q = 0; q < ns; ++q) {
+    const double W = std::fabs(omegas[f0 + q]);
+    dT[q] = W > 0.0 ? std::min(T, two_pi / W) : T;
+    K[q] = std::max(1, (int)std::floor(T / dT[q] + 1e-12));
+    rem[q] = T - K[q] * dT[q];
+    if (rem[q] > 1e-12 * T) has_r[q] = 1;
+    else rem[q] = 0.0;
+    Kmax = std::max(Kmax, K[q]);
+  }
+  // w2 over one period, and over the remainder, from zero (plain method)
+  for (int q = 0; q < ns; ++q)
+    KX_CUDA(c, cudaMemsetAsync(slot_col(c, q, 0), 0, vb, c->stream), "zero w2");
+  KX_TRY(slots_time_loop(c, ns, true, d_g, omegas, f0, rtol, eta, dT, all, err));
+  for (int q = 0; q < ns; ++q) {
+    KX_CUDA(c, cudaMemcpyAsync(vec_ptr(c, c->d_zre, f0 + q), slot_col(c, q, 0), vb, cudaMemcpyDeviceToDevice,
+                               c->stream), "keep w2");
+    KX_CUDA(c, cudaMemsetAsync(slot_col(c, q, 0), 0, vb, c->stream), "zero w2");
+  }
+  KX_TRY(slots_time_loop(c, ns, true, d_g, omegas, f0, rtol, eta, rem, has_r, err));
+  for (int q = 0; q < ns; ++q)
+    if (has_r[q])
+      KX_CUDA(c, cudaMemcpyAsync(vec_ptr(c, c->d_zim, f0 + q), slot_col(c, q, 0), vb, cudaMemcpyDeviceToDevice,
+                                 c->stream), "keep w2 of the remainder");
+  // y(dT) = w2; y(k dT) = exp(-dT A) y((k-1) dT) + w2 for k = 2 .. K
+  for (int q = 0; q < ns; ++q)
+    KX_CUDA(c, cudaMemcpyAsync(slot_col(c, q, 0), vec_ptr(c, c->d_zre, f0 + q), vb, cudaMemcpyDeviceToDevice,
+                               c->stream), "y = w2");
+  for (int k = 2; k <= Kmax; ++k) {
+    std::vector<char> on(ns);
+    for (int q = 0; q < ns; ++q) on[q] = k <= K[q];
+    KX_TRY(slots_time_loop(c, ns, false, nullptr, omegas, f0, rtol, eta, dT, on, err));
+    for (int q = 0; q < ns; ++q)
+      if (on[q]) KX_TRY(launch_axpy(c, 1.0, vec_ptr(c, c->d_zre, f0 + q), slot_col(c, q, 0)));
+  }
+  // the last, shorter subinterval
+  KX_TRY(slots_time_loop(c, ns, false, nullptr, omegas, f0, rtol, eta, rem, has_r, err));
+  for (int q = 0; q < ns; ++q)
+    if (has_r[q]) KX_TRY(launch_axpy(c, 1.0, vec_ptr(c, c->d_zim, f0 + q), slot_col(c, q, 0)));
+  if (err_est)
+    for (int q = 0; q < ns; ++q) err_est[f0 + q] = err[q];
+  return sync(c);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -646,7 +738,9 @@ kx_status response_at_freqs(kx_ctx* c, const void* d_g, const double* omegas, in
   if (method == KX_RSTDIM)
     return response_restart_dim(c, d_g, omegas, nfreq, T, rtol, 0.0, 0, plane, d_E_plane, intensity, err_est,
                                 nullptr, d_Y);
-  if (method != KX_PLAIN && method != KX_SPLIT) return fail(c, KX_EINVAL, "bad method");
+  if (method != KX_PLAIN && method != KX_SPLIT && method != KX_SPLIT2 && method != KX_SPLIT4D)
+    return fail(c, KX_EINVAL, "bad method");
+  const bool split = method == KX_SPLIT || method == KX_SPLIT4D;   // eq. (split1): stationary + transient
   if (!plane) return fail(c, KX_EINVAL, "plane is NULL");
   const int axis = plane[0], idx = plane[1];
   if (axis < 0 || axis >= c->d.dim) return fail(c, KX_EINVAL, "bad plane axis");
@@ -659,7 +753,7 @@ kx_status response_at_freqs(kx_ctx* c, const void* d_g, const double* omegas, in
   const int slot = 0;
   kx_status conv = KX_OK;
   double* d_int = c->d_small + 128;
-  if (method == KX_SPLIT) {
+  if (split) {
     // Fig. alg:spl1, steps 1-3 for every frequency, with all stationary
     // parts from one shifted solve (Corollary 1 applied to z_stat).
     kx_status st = stationary_core(c, d_g, omegas, nfreq, rtol * 0.1, 400 * c->m, c->d_zre,
@@ -678,8 +772,65 @@ kx_status response_at_freqs(kx_ctx* c, const void* d_g, const double* omegas, in
   const double gnorm = gst.beta;
   // frequencies advance in waves of up to `batch` slots sharing every launch
   const int B = c->d.batch;
+  const size_t vb = (size_t)c->n * c->esize;
   for (int f0 = 0; f0 < nfreq; f0 += B) {
     const int ns = std::min(B, nfreq - f0);
+    if (method == KX_SPLIT2) {
+      KX_TRY(split2_wave(c, d_g, omegas, f0, ns, T, rtol, gnorm > 0.0 ? gnorm : 1.0, err_est));
+      for (int q = 0; q < ns; ++q) {
+        const int f = f0 + q;
+        void* Ep = d_E_plane ? (char*)d_E_plane + (int64_t)f * nE * np * c->esize : nullptr;
+        void* Yf = d_Y ? vec_ptr(c, d_Y, f) : nullptr;
+        KX_TRY(launch_response(c, f, omegas, T, 0, nullptr, nullptr, slot_col(c, q, 0), axis, idx, Ep, d_int + f,
+                               Yf));
+      }
+      continue;
+    }
+    if (method == KX_SPLIT4D) {
+      // eq. (4diff): slot q carries Im z_f - Im z_{f-1} (f >= 1), solved to
+      // the tolerance of Im z_f itself (its norm from a first pass)
+      for (int q = 0; q < ns; ++q) {
+        KX_CUDA(c, cudaMemcpyAsync(slot_col(c, q, 0), vec_ptr(c, c->d_zim, f0 + q), vb, cudaMemcpyDeviceToDevice,
+                                   c->stream), "copy Im z");
+        c->h_state[q] = fresh_state();
+      }
+      KX_CUDA(c, cudaMemcpyAsync(c->d_state, c->h_state, sizeof(SlotState) * ns, cudaMemcpyHostToDevice,
+                                 c->stream), "state upload");
+      KX_TRY(launch_norm_init(c, 0, ns));
+      KX_TRY(read_states(c, 0, ns));
+      std::vector<double> znorm(ns);
+      for (int q = 0; q < ns; ++q) znorm[q] = c->h_state[q].beta;
+      for (int q = 0; q < ns; ++q) {
+        const int f = f0 + q;
+        if (f >= 1) KX_TRY(launch_axpy(c, -1.0, vec_ptr(c, c->d_zim, f - 1), slot_col(c, q, 0)));
+        SlotState s = fresh_state();
+        s.T = T;
+        s.rtol = rtol;
+        s.tol_mode = 0;
+        if (znorm[q] > 0.0) s.tol_abs = rtol * znorm[q] / T;
+        c->h_state[q] = s;
+      }
+      KX_CUDA(c, cudaMemcpyAsync(c->d_state, c->h_state, sizeof(SlotState) * ns, cudaMemcpyHostToDevice,
+                                 c->stream), "state upload");
+      KX_TRY(sync(c));
+      KX_TRY(time_loop(c, 0, ns, nullptr, err_est ? err_est + f0 : nullptr));
+      // yhat_f(T) = yhat_{f-1}(T) + w_f(T)  (Fig. alg:spl1 steps 5-6); the
+      // previous wave's last transient waits in d_tmp
+      for (int q = 0; q < ns; ++q) {
+        const int f = f0 + q;
+        if (f >= 1) KX_TRY(launch_axpy(c, 1.0, q == 0 ? c->d_tmp : slot_col(c, q - 1, 0), slot_col(c, q, 0)));
+      }
+      KX_CUDA(c, cudaMemcpyAsync(c->d_tmp, slot_col(c, ns - 1, 0), vb, cudaMemcpyDeviceToDevice, c->stream),
+              "keep the last transient");
+      for (int q = 0; q < ns; ++q) {
+        const int f = f0 + q;
+        void* Ep = d_E_plane ? (char*)d_E_plane + (int64_t)f * nE * np * c->esize : nullptr;
+        void* Yf = d_Y ? vec_ptr(c, d_Y, f) : nullptr;
+        KX_TRY(launch_response(c, f, omegas, T, 1, vec_ptr(c, c->d_zre, f), vec_ptr(c, c->d_zim, f),
+                               slot_col(c, q, 0), axis, idx, Ep, d_int + f, Yf));
+      }
+      continue;
+    }
     for (int q = 0; q < ns; ++q) {
       const int f = f0 + q;
       SlotState s = fresh_state();

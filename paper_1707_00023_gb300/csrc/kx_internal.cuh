@@ -229,6 +229,8 @@ int gauss_points();
 kx_status launch_norm_init(kx_ctx* c, int slot0, int ns);
 kx_status launch_combine(kx_ctx* c, int slot0, int ns);
 kx_status launch_basis_export(kx_ctx* c, int slot, void* dV, int m);
+// y += a x, n scalars of the context's precision
+kx_status launch_axpy(kx_ctx* c, double a, const void* x, void* y);
 kx_status launch_zupdate(kx_ctx* c, int slot, int nfreq, void* zre, void* zim, int m);
 kx_status launch_true_residual(kx_ctx* c, const void* g, int nfreq, const double* d_om,
                                void* zre, void* zim, double* out_host);

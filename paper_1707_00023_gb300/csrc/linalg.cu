@@ -352,6 +352,25 @@ kx_status launch_combine(kx_ctx* c, int slot, int ns) {
 }
 
 // ---------------------------------------------------------------------------
+// y += a x over n scalars (the periodic-source methods combine whole fields).
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_axpy(int64_t n, double a, const T* __restrict__ x, T* __restrict__ y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = (T)((double)y[e] + a * (double)x[e]);
+}
+
+kx_status launch_axpy(kx_ctx* c, double a, const void* x, void* y) {
+  time_begin(c);
+  if (c->d.precision == KX_FP64)
+    k_axpy<double><<<c->nblk, NTHREADS, 0, c->stream>>>(c->n, a, (const double*)x, (double*)y);
+  else
+    k_axpy<float><<<c->nblk, NTHREADS, 0, c->stream>>>(c->n, a, (const float*)x, (float*)y);
+  time_end(c, KX_K_RESTART, 3.0 * c->n * c->esize);
+  KX_CHECK_LAUNCH(c);
+  return KX_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Export the orthonormal basis: dV[:, i] = scale_i V_i (i <= m_done, and the
 // column past a lucky breakdown is zero).
 template <typename T>
