@@ -55,6 +55,16 @@ WORKLOADS = {
     "3d128_32f_T400_rst": dict(dim=3, n=128, seed=1710, fill=0.3, T=400.0, m=64, nfreq=32,
                                prec="fp32", method="rstdim", rtol=1e-7, t_oracle=4.0, rst_samples=4096,
                                batch=2),
+    # source splitting (eq. (split2)) on the 64^3 medium, 32 frequencies in lockstep
+    "3d64_m64_T400_32f_split2": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=32,
+                                     prec="fp32", method="split2", rtol=1e-7, t_oracle=20.0, batch=32),
+    # the neighbouring-frequency difference (eq. (4diff)) against the plain
+    # split, on a 2D cavity whose stationary parts converge: 8 frequencies
+    # 0.001 Omega0 apart (the paper's step)
+    "2d12_m40_T60_8f_split4d": dict(dim=2, n=12, ndisks=2, seed=1708, T=60.0, m=40, nfreq=8, prec="fp64",
+                                    method="split4d", rtol=1e-11, t_oracle=60.0, batch=8, band=(1.0, 1.007)),
+    "2d12_m40_T60_8f_split": dict(dim=2, n=12, ndisks=2, seed=1708, T=60.0, m=40, nfreq=8, prec="fp64",
+                                  method="split", rtol=1e-11, t_oracle=60.0, batch=8, band=(1.0, 1.007)),
     # 2D 64^2, 40 disks, FP64, m = 30, T = 200, plain method
     "2d64_m30_T200": dict(dim=2, n=64, seed=1708, T=200.0, m=30, nfreq=1, prec="fp64",
                           method="plain", rtol=1e-11, t_oracle=200.0),
@@ -83,10 +93,11 @@ def shard_frequencies(nfreq, rank, world, lo=0.8, hi=1.2):
 def scenario_for(w, rank=0, world=1):
     import scenario as S
     if w["dim"] == 2:
-        sc = S.config_2d(n=w["n"], seed=w["seed"], T=w["T"], m=w["m"])
+        sc = S.config_2d(n=w["n"], seed=w["seed"], T=w["T"], m=w["m"], ndisks=w.get("ndisks", 40))
     else:
         sc = S.config_3d(n=w["n"], seed=w["seed"], fill=w["fill"], T=w["T"], m=w["m"])
-    sc.omegas = shard_frequencies(w["nfreq"], rank, world) if w["nfreq"] > 1 else S.freq_list(1)
+    lo, hi = w.get("band", (0.8, 1.2))
+    sc.omegas = shard_frequencies(w["nfreq"], rank, world, lo, hi) if w["nfreq"] > 1 else S.freq_list(1)
     return sc
 
 

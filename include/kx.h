@@ -191,7 +191,8 @@ kx_status expm_action(kx_ctx* ctx, const void* d_y0, double T, double rtol,
  *   method KX_SPLIT4D: as KX_SPLIT, but the transient of each frequency
  *     after the first comes from the previous one's (eq. (4diff), Fig.
  *     alg:spl1 steps 4-6): yhat_j(T) = yhat_{j-1}(T) + exp(-TA)(Im z_j -
- *     Im z_{j-1}), the difference solved to the tolerance of Im z_j itself;
+ *     Im z_{j-1}), each difference solved to rtol ||Im z_j|| / nfreq (so the
+ *     errors that frequency j accumulates stay within its own budget);
  *     frequencies are taken in the given order (neighbours should be close).
  *   plane: host int[2] = {axis, index}: output plane perpendicular to axis.
  *   d_E_plane: device, nfreq x nE x (plane nodes) scalars (nE = 1 in 2D:

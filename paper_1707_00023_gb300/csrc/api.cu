@@ -788,7 +788,7 @@ kx_status response_at_freqs(kx_ctx* c, const void* d_g, const double* omegas, in
     }
     if (method == KX_SPLIT4D) {
       // eq. (4diff): slot q carries Im z_f - Im z_{f-1} (f >= 1), solved to
-      // the tolerance of Im z_f itself (its norm from a first pass)
+      // a tolerance relative to Im z_f itself (its norm from a first pass)
       for (int q = 0; q < ns; ++q) {
         KX_CUDA(c, cudaMemcpyAsync(slot_col(c, q, 0), vec_ptr(c, c->d_zim, f0 + q), vb, cudaMemcpyDeviceToDevice,
                                    c->stream), "copy Im z");
@@ -807,7 +807,9 @@ kx_status response_at_freqs(kx_ctx* c, const void* d_g, const double* omegas, in
         s.T = T;
         s.rtol = rtol;
         s.tol_mode = 0;
-        if (znorm[q] > 0.0) s.tol_abs = rtol * znorm[q] / T;
+        // frequency f sums the errors of the f differences before it: each
+        // difference gets 1/nfreq of the budget rtol ||Im z_f||
+        if (znorm[q] > 0.0) s.tol_abs = rtol * znorm[q] / (T * (f >= 1 ? nfreq : 1));
         c->h_state[q] = s;
       }
       KX_CUDA(c, cudaMemcpyAsync(c->d_state, c->h_state, sizeof(SlotState) * ns, cudaMemcpyHostToDevice,
