@@ -25,6 +25,8 @@ arXiv:1707.00023 it follows):
 * ``periodic`` -- the two uses of the source's periodicity (Sect. 3.5):
                   source splitting, eq. (split2), and the neighbouring-
                   frequency difference, eq. (4diff) in Fig. alg:spl1.
+* ``pml``      -- the paper's 2D model with the perfectly matched layer
+                  (auxiliary field P, eq. (mxw); block form of eq. (ode)).
 * ``adjoint``  -- gradient of the output-plane intensity with respect to
                   per-cell permittivity (no counterpart in the paper).
 

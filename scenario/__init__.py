@@ -93,7 +93,9 @@ class Grid:
     ``n`` = cells per axis (x, y[, z]).  ``bc[a]`` is PEC or PERIODIC for axis
     a.  The absorbing layer lies inside the grid at both ends of
     ``layer_axis`` and is ``layer_cells`` thick; ``sigma_max`` is its peak
-    conductivity (linear ramp).
+    conductivity (linear ramp).  ``pml = 1`` (2D, layer along x) selects the
+    paper's perfectly matched layer instead: a fourth field P on the Ez
+    nodes and a quadratic conductivity profile.
     """
 
     dim: int
@@ -102,6 +104,7 @@ class Grid:
     layer_axis: int
     layer_cells: int
     sigma_max: float
+    pml: int = 0
 
     @property
     def ncell(self) -> int:
@@ -109,7 +112,7 @@ class Grid:
 
     @property
     def ncomp(self) -> int:
-        return 3 if self.dim == 2 else 6
+        return (3 + self.pml) if self.dim == 2 else 6
 
     @property
     def nunk(self) -> int:
@@ -252,7 +255,7 @@ def source_2d(grid: Grid, ix: int) -> np.ndarray:
     """
     nx, ny = grid.n
     g = np.zeros(grid.nunk)
-    ez = g[2 * grid.ncell:].reshape(ny, nx)
+    ez = g[2 * grid.ncell:3 * grid.ncell].reshape(ny, nx)
     edge = ny / 10.0
     for j in range(ny):
         y = float(j)
@@ -294,6 +297,20 @@ def config_2d(n=64, seed=1708, ndisks=40, T=200.0, m=30, omegas=None) -> Scenari
     g = source_2d(grid, xs)
     om = np.array([OMEGA0]) if omegas is None else np.asarray(omegas, float)
     return Scenario(grid, eps, g, om, T, m, (0, xo), f"2d_n{n}", disks, ov)
+
+
+def config_2d_pml(n=64, seed=1708, ndisks=40, T=200.0, m=30, omegas=None, sigma_max=3.0) -> Scenario:
+    """The medium and source of ``config_2d`` with the paper's perfectly
+    matched layer (auxiliary field P, quadratic conductivity rising to
+    sigma_max over the 6-cell layer at both x ends) instead of the lossy
+    layer."""
+    sc = config_2d(n=n, seed=seed, ndisks=ndisks, T=T, m=m, omegas=omegas)
+    g0 = sc.grid
+    grid = Grid(2, g0.n, g0.bc, g0.layer_axis, g0.layer_cells, sigma_max, pml=1)
+    g = np.zeros(grid.nunk)
+    g[:g0.nunk] = sc.g
+    return Scenario(grid, sc.eps_cell, g, sc.omegas, T, m, sc.plane, f"2d_pml_n{n}", sc.inclusions,
+                    sc.overlap_allowed_after)
 
 
 def config_3d(n=64, seed=1709, fill=0.3, T=400.0, m=64, omegas=None,
@@ -355,7 +372,9 @@ def component_offsets(dim: int):
 def wall_keep_mask(grid: Grid) -> np.ndarray:
     """1 for unknowns of the system, 0 for nodes on a conducting wall."""
     keep = np.ones((grid.ncomp,) + grid.shape)
-    offs = component_offsets(grid.dim)
+    offs = list(component_offsets(grid.dim))
+    if grid.dim == 2 and grid.pml:
+        offs.append(offs[2])          # P lives on the Ez nodes
     for c in range(grid.ncomp):
         for a in range(grid.dim):
             if grid.bc[a] == PEC and offs[c][a] == 0.0:
