@@ -76,6 +76,14 @@ typedef struct {
                          restart-in-dimension method (0: method unavailable);
                          the workspace is max_freqs * rst_samples * 72
                          bytes plus max_freqs output-plane accumulators      */
+  int pml;            /* 0: lossy layer (above).  1: the paper's perfectly
+                         matched layer (2D, layer_axis 0 only; Sect. 2.1,
+                         eq. (mxw)): fields [Hx, Hy, Ez, P] with P on the Ez
+                         nodes, Hy' = dEz/dx - sigma Hy, Ez' = (dHy/dx -
+                         dHx/dy)/eps - sigma Ez + P, P' = -(sigma/eps) dHx/dy,
+                         sigma = sigma_max (d/L)^2 damping Hy and Ez only.
+                         n = 4 ncell; the output plane holds Ez; the adjoint
+                         and kx_arnoldi_noalloc reject it                    */
 } kx_desc;
 
 typedef struct kx_ctx kx_ctx;

@@ -44,7 +44,7 @@ class Desc(ctypes.Structure):
                 ("layer_axis", ctypes.c_int), ("layer_cells", ctypes.c_int),
                 ("sigma_max", ctypes.c_double), ("precision", ctypes.c_int),
                 ("krylov_dim", ctypes.c_int), ("max_freqs", ctypes.c_int), ("batch", ctypes.c_int),
-                ("max_checkpoints", ctypes.c_int), ("rst_samples", ctypes.c_int)]
+                ("max_checkpoints", ctypes.c_int), ("rst_samples", ctypes.c_int), ("pml", ctypes.c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -118,7 +118,7 @@ class Context:
     """One solver context: grid, permittivity, precision and workspace.
 
     ``grid`` is any object with attributes dim, n, bc, layer_axis,
-    layer_cells, sigma_max (e.g. ``scenario.Grid``).  ``eps_cell`` is the
+    layer_cells, sigma_max and optionally pml (e.g. ``scenario.Grid``).  ``eps_cell`` is the
     per-cell permittivity (numpy, x fastest).  ``stream``: a torch CUDA
     stream (default: the current stream), or ``"own"`` for a private stream
     created by the library (distinct per context; use it for concurrent
@@ -149,6 +149,7 @@ class Context:
         d.batch = batch
         d.max_checkpoints = max_checkpoints
         d.rst_samples = rst_samples
+        d.pml = int(getattr(grid, "pml", 0))
         self.desc = d
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         own = isinstance(stream, str) and stream == "own"

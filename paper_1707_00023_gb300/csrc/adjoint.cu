@@ -32,7 +32,7 @@ constexpr double QUAD_DELTA = 0.4;  // longest sub-interval (time units)
 // lambda(T) = 2 P^T P y: plane values of the E components, zero elsewhere.
 template <typename T>
 __global__ void k_adj_seed(Geo g, int axis, int idx, const T* __restrict__ y, T* __restrict__ lam) {
-  const int nE = g.ncomp - g.nh;
+  const int nE = g.ne;
   int na, nb;
   if (g.dim == 2) {
     na = axis == 0 ? g.ny : g.nx;
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(NTHREADS) k_adj_accum(Geo g, const T* __restri
   __shared__ float sa[CH][MMAX + 1];
   __shared__ float so[CH][MMAX];
   __shared__ float scw[CH], ssn[CH];
-  const int64_t nE = (int64_t)(g.ncomp - g.nh) * g.ncell;
+  const int64_t nE = (int64_t)g.ne * g.ncell;
   const int64_t off = (int64_t)g.nh * g.ncell;
   const int64_t rounds = (nE + blockDim.x - 1) / blockDim.x;
   for (int64_t r0 = blockIdx.x; r0 < rounds; r0 += gridDim.x) {
@@ -334,7 +334,7 @@ kx_status launch_adj_substep(kx_ctx* c, double tau, double omega, double tk, con
   time_end(c, KX_K_PROJ, 0.0);
   KX_CHECK_LAUNCH(c);
   const int nq = nsub * GAUSS_P;
-  const int64_t nE = (int64_t)(c->geo.ncomp - c->geo.nh) * c->geo.ncell;
+  const int64_t nE = (int64_t)c->geo.ne * c->geo.ncell;
   const int blocks = (int)std::min<int64_t>((nE + NTHREADS - 1) / NTHREADS, (int64_t)c->nsm * 4);
   const int64_t sV = (int64_t)(m + 1) * c->ld;
   // the basis sizes are read back by the host after each Arnoldi run

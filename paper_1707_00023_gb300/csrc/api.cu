@@ -210,7 +210,7 @@ kx_status check_plane(kx_ctx* c, const int* plane, int* axis, int* idx, int64_t*
   if (*idx < 0 || *idx >= na) return fail(c, KX_EINVAL, "bad plane index");
   int a = 0, b = 0;
   plane_dims(c->geo, *axis, &a, &b);
-  *P = (int64_t)(c->geo.ncomp - c->geo.nh) * a * b;
+  *P = (int64_t)c->geo.ne * a * b;
   return KX_OK;
 }
 
@@ -402,6 +402,10 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
   if (d.max_checkpoints < 0 || (d.max_checkpoints > 0 && d.batch < 2))
     return fail(nullptr, KX_EINVAL, "max_checkpoints must be >= 0, and the adjoint needs batch >= 2");
   if (d.rst_samples < 0 || d.rst_samples > (1 << 24)) return fail(nullptr, KX_EINVAL, "rst_samples must be 0 .. 2^24");
+  if (d.pml != 0 && d.pml != 1) return fail(nullptr, KX_EINVAL, "pml must be 0 or 1");
+  if (d.pml && (d.dim != 2 || d.layer_axis != 0))
+    return fail(nullptr, KX_EINVAL, "the PML model is 2D with the layer along x (layer_axis 0)");
+  if (d.pml && d.max_checkpoints > 0) return fail(nullptr, KX_EINVAL, "the adjoint does not cover the PML model");
   const int nz = d.dim == 3 ? d.n[2] : 1;
   const int64_t ncell = (int64_t)d.n[0] * d.n[1] * nz;
   for (int64_t i = 0; i < ncell; ++i)
@@ -428,11 +432,13 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
   g.ny = d.n[1];
   g.nz = nz;
   g.ncell = ncell;
-  g.ncomp = d.dim == 2 ? 3 : 6;
+  g.pml = d.pml;
+  g.ncomp = d.dim == 2 ? 3 + d.pml : 6;
   g.nh = d.dim == 2 ? 2 : 3;
+  g.ne = d.dim == 2 ? 1 : 3;
   g.la = d.layer_axis;
-  // staggered offsets: 1 = half-integer along the axis
-  static const int off2[3][3] = {{0, 1, 0}, {1, 0, 0}, {0, 0, 0}};
+  // staggered offsets: 1 = half-integer along the axis (P: on the Ez nodes)
+  static const int off2[4][3] = {{0, 1, 0}, {1, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   static const int off3[6][3] = {{0, 1, 1}, {1, 0, 1}, {1, 1, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
   for (int comp = 0; comp < g.ncomp; ++comp) {
     const int* off = d.dim == 2 ? off2[comp] : off3[comp];
@@ -462,7 +468,7 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
   const int nla = d.n[d.layer_axis];
   size_t bytes_V = (size_t)B * (m + 1) * c->ld * c->esize;
   struct Alloc { void** p; size_t bytes; } allocs[] = {
-      {(void**)&c->d_inv_eps, (size_t)(g.ncomp - g.nh) * ncell * c->esize},
+      {(void**)&c->d_inv_eps, (size_t)g.ne * ncell * c->esize},
       {(void**)&c->d_sig2, (size_t)2 * nla * c->esize},
       {(void**)&c->d_eps_cell, (size_t)ncell * sizeof(double)},
       {(void**)&c->d_V, bytes_V},
@@ -495,7 +501,7 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
   if (d.max_checkpoints > 0) {
     const int P = gauss_points();
     c->adj_nq_max = 64 * P;
-    const int64_t nE = (int64_t)(g.ncomp - g.nh) * ncell;
+    const int64_t nE = (int64_t)g.ne * ncell;
     Alloc adj[] = {
         {(void**)&c->d_ckpt, (size_t)d.max_checkpoints * c->ld * c->esize},
         {(void**)&c->d_adj_Q, (size_t)nE * sizeof(double)},
@@ -528,7 +534,7 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
       plane_dims(g, a, &na, &nb);
       pmax = std::max<int64_t>(pmax, (int64_t)na * nb);
     }
-    c->rst_plane_max = (int64_t)(g.ncomp - g.nh) * pmax;
+    c->rst_plane_max = (int64_t)g.ne * pmax;
     Alloc rst[] = {
         {(void**)&c->d_rst_b, (size_t)d.max_freqs * d.rst_samples * RST_P * sizeof(double)},
         {(void**)&c->d_rst_smp, (size_t)d.max_freqs * (d.rst_samples + 1) * 3 * sizeof(double)},
@@ -749,7 +755,7 @@ kx_status response_at_freqs(kx_ctx* c, const void* d_g, const double* omegas, in
   int64_t np = 1;
   for (int a = 0; a < c->d.dim; ++a)
     if (a != axis) np *= c->d.n[a];
-  const int nE = c->geo.ncomp - c->geo.nh;
+  const int nE = c->geo.ne;
   const int slot = 0;
   kx_status conv = KX_OK;
   double* d_int = c->d_small + 128;
@@ -1072,7 +1078,7 @@ kx_status adjoint_response_grad(kx_ctx* c, const void* d_g, const double* omegas
   if (axis < 0 || axis >= c->d.dim) return fail(c, KX_EINVAL, "bad plane axis");
   const int na = axis == 0 ? c->geo.nx : (axis == 1 ? c->geo.ny : c->geo.nz);
   if (idx < 0 || idx >= na) return fail(c, KX_EINVAL, "bad plane index");
-  const int64_t nE = (int64_t)(c->geo.ncomp - c->geo.nh) * c->geo.ncell;
+  const int64_t nE = (int64_t)c->geo.ne * c->geo.ncell;
   KX_CUDA(c, cudaMemsetAsync(c->d_adj_Q, 0, (size_t)nE * sizeof(double), c->stream), "zero Q");
   // ||g|| balances the augmented phase entries (as in response_at_freqs)
   KX_CUDA(c, cudaMemcpyAsync(slot_col(c, 0, 0), d_g, c->n * c->esize, cudaMemcpyDeviceToDevice, c->stream),

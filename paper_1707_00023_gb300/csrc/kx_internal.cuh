@@ -24,6 +24,8 @@ struct Geo {
   int dim, nx, ny, nz;
   int64_t ncell;
   int ncomp, nh;
+  int ne;                // E field components (1 in 2D, 3 in 3D)
+  int pml;               // 1: 2D with the auxiliary PML field P as component 3
   unsigned maskbits[6];  // bit a set: node index 0 along axis a is a wall node
   int la;                // layer axis
   int sighalf[6];        // 1 if the component is half-integer along la

@@ -103,13 +103,48 @@ struct CellMat {
 };
 
 
+// Stored components per cell of a model: DIM = 2 (Hx, Hy, Ez), 3 (the six
+// 3D fields), 4 (2D with the PML field P: Hx, Hy, Ez, P).
+__host__ __device__ constexpr int ncomp_of(int DIM) { return DIM == 3 ? 6 : (DIM == 4 ? 4 : 3); }
+
 // out = A v (TR = 0) or A^T v (TR = 1) at the components of one cell.
+// DIM = 4 is the paper's 2D PML model (eq. (mxw)): sigma damps Hy and Ez at
+// the same rate (not divided by eps), Ez' gains + P and
+// P' = -(sigma / eps) dHx/dy, so the rows are
+//   Hx: dEz/dy    Hy: sigma Hy - dEz/dx    Ez: sigma Ez - curl H / eps - P
+//   P:  (sigma / eps) dHx/dy
+// and A^T follows the blocks (with u = (w_Ez + sigma w_P) / eps on the Ez
+// nodes): Hx: -du/dy, Hy: sigma w_Hy + d(w_Ez/eps)/dx, Ez: sigma w_Ez + curl
+// w_H, P: -w_Ez.  sigma depends on x only.
 template <typename T, int DIM, int TR, typename Mat>
 __device__ __forceinline__ void stencil(const Geo& g, const T* __restrict__ v, const Mat& mat,
                                         const Cell& q, T* out) {
   const int64_t nc = g.ncell;
   const int i = q.i, j = q.j, k = q.k;
-  if (DIM == 2) {
+  if (DIM == 4) {
+    (void)nc;
+    const T Hx = ldv(g, v, 0, q.c0, i, j, k), Hy = ldv(g, v, 1, q.c0, i, j, k);
+    const T Hy_im = ldv(g, v, 1, q.cim, q.im, j, k), Hx_jm = ldv(g, v, 0, q.cjm, i, q.jm, k);
+    const T Ez = ldv(g, v, 2, q.c0, i, j, k), P = ldv(g, v, 3, q.c0, i, j, k);
+    const T Ez_jp = ldv(g, v, 2, q.cjp, i, q.jp, k), Ez_ip = ldv(g, v, 2, q.cip, q.ip, j, k);
+    const T sH = mat.sigma(g, q, 1), sE = mat.sigma(g, q, 2);
+    const T ie0 = mat.inv_eps(g, 0, q.c0);
+    const T curlH = (Hy - Hy_im) - (Hx - Hx_jm);
+    if (!TR) {
+      out[0] = Ez_jp - Ez;
+      out[1] = sH * Hy - (Ez_ip - Ez);
+      out[2] = sE * Ez - ie0 * curlH - P;
+      out[3] = sE * ie0 * (Hx - Hx_jm);
+    } else {
+      const T P_jp = ldv(g, v, 3, q.cjp, i, q.jp, k);
+      const T u = (Ez + sE * P) * ie0;
+      const T u_jp = (Ez_jp + sE * P_jp) * mat.inv_eps(g, 0, q.cjp);
+      out[0] = -(u_jp - u);
+      out[1] = sH * Hy + (Ez_ip * mat.inv_eps(g, 0, q.cip) - Ez * ie0);
+      out[2] = sE * Ez + curlH;
+      out[3] = -Ez;
+    }
+  } else if (DIM == 2) {
     // components 0 Hx (0,1/2), 1 Hy (1/2,0), 2 Ez (0,0)
     const T Hx = ldv(g, v, 0, q.c0, i, j, k), Hy = ldv(g, v, 1, q.c0, i, j, k);
     const T Hy_im = ldv(g, v, 1, q.cim, q.im, j, k), Hx_jm = ldv(g, v, 0, q.cjm, i, q.jm, k);
@@ -172,7 +207,7 @@ __device__ __forceinline__ void stencil(const Geo& g, const T* __restrict__ v, c
       out[5] = s[5] * Ez + cHz;
     }
   }
-  constexpr int NC = DIM == 2 ? 3 : 6;
+  constexpr int NC = ncomp_of(DIM);
 #pragma unroll
   for (int c = 0; c < NC; ++c)
     if (is_wall(g, c, i, j, k)) out[c] = T(0);

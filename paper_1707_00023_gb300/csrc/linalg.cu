@@ -524,7 +524,7 @@ template <typename T>
 __global__ void k_plane(Geo g, int split, double sW, double cW, const T* __restrict__ zr,
                         const T* __restrict__ zi, const T* __restrict__ yt, int axis, int idx,
                         T* __restrict__ E_plane, double* intensity) {
-  const int nE = g.ncomp - g.nh;
+  const int nE = g.ne;
   int na, nb;
   plane_dims(g, axis, &na, &nb);
   const int64_t np = (int64_t)na * nb;

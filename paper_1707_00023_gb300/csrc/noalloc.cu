@@ -90,6 +90,7 @@ extern "C" kx_status kx_arnoldi_noalloc(const kx_desc* desc, const double* d_eps
       2 * d.layer_cells > d.n[d.layer_axis] || !(d.sigma_max >= 0.0))
     return err(KX_EINVAL, "bad absorbing layer");
   if (d.precision != KX_FP64 && d.precision != KX_FP32) return err(KX_EINVAL, "bad precision");
+  if (d.pml != 0) return err(KX_EINVAL, "the PML model is not available here (pml must be 0)");
   const int esize = d.precision == KX_FP64 ? 8 : 4;
   const int nz = d.dim == 3 ? d.n[2] : 1;
   const int64_t ncell = (int64_t)d.n[0] * d.n[1] * nz;
@@ -121,6 +122,7 @@ extern "C" kx_status kx_arnoldi_noalloc(const kx_desc* desc, const double* d_eps
   g.ncell = ncell;
   g.ncomp = ncomp;
   g.nh = d.dim == 2 ? 2 : 3;
+  g.ne = d.dim == 2 ? 1 : 3;
   g.la = d.layer_axis;
   static const int off2[3][3] = {{0, 1, 0}, {1, 0, 0}, {0, 0, 0}};
   static const int off3[6][3] = {{0, 1, 1}, {1, 0, 1}, {1, 1, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};

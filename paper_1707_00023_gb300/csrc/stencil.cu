@@ -21,7 +21,7 @@ namespace kx {
 template <typename T>
 __global__ void k_setup_inv_eps(Geo g, const double* __restrict__ eps, T* __restrict__ ie) {
   const int64_t nc = g.ncell;
-  const int nE = g.ncomp - g.nh;
+  const int nE = g.ne;
   const int64_t nxy = (int64_t)g.nx * g.ny;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nE * nc;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -48,18 +48,20 @@ __global__ void k_setup_inv_eps(Geo g, const double* __restrict__ eps, T* __rest
   }
 }
 
+// Lossy layer: linear ramp sigma_max d / L; PML: quadratic sigma_max (d/L)^2
+// (Sect. 4.1).
 template <typename T>
-__global__ void k_setup_sig(T* sig2, int n, int L, double smax) {
+__global__ void k_setup_sig(T* sig2, int n, int L, double smax, int quad) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * n) return;
   const double pos = 0.5 * t;
-  double d = fmax(fmax((double)L - pos, pos - (double)(n - L)), 0.0);
-  sig2[t] = (T)(smax * d / (double)L);
+  const double r = fmax(fmax((double)L - pos, pos - (double)(n - L)), 0.0) / (double)L;
+  sig2[t] = (T)(smax * (quad ? r * r : r));
 }
 
 kx_status launch_setup_material(kx_ctx* c) {
   const Geo& g = c->geo;
-  const int nE = g.ncomp - g.nh;
+  const int nE = g.ne;
   const int64_t tot = nE * g.ncell;
   const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 65535);
   const int nla = g.la == 0 ? g.nx : (g.la == 1 ? g.ny : g.nz);
@@ -67,12 +69,12 @@ kx_status launch_setup_material(kx_ctx* c) {
     k_setup_inv_eps<double><<<blocks, 256, 0, c->stream>>>(g, c->d_eps_cell, (double*)c->d_inv_eps);
     KX_CHECK_LAUNCH(c);
     k_setup_sig<double><<<(2 * nla + 255) / 256, 256, 0, c->stream>>>(
-        (double*)c->d_sig2, nla, c->d.layer_cells, c->d.sigma_max);
+        (double*)c->d_sig2, nla, c->d.layer_cells, c->d.sigma_max, g.pml);
   } else {
     k_setup_inv_eps<float><<<blocks, 256, 0, c->stream>>>(g, c->d_eps_cell, (float*)c->d_inv_eps);
     KX_CHECK_LAUNCH(c);
     k_setup_sig<float><<<(2 * nla + 255) / 256, 256, 0, c->stream>>>(
-        (float*)c->d_sig2, nla, c->d.layer_cells, c->d.sigma_max);
+        (float*)c->d_sig2, nla, c->d.layer_cells, c->d.sigma_max, g.pml);
   }
   KX_CHECK_LAUNCH(c);
   return KX_OK;
@@ -83,7 +85,7 @@ kx_status launch_setup_material(kx_ctx* c) {
 template <typename T, int DIM, int TR>
 __global__ void __launch_bounds__(NTHREADS) k_apply(Geo g, const T* __restrict__ v, T* __restrict__ w,
                                                    const T* __restrict__ ie, const T* __restrict__ sig2) {
-  constexpr int NC = DIM == 2 ? 3 : 6;
+  constexpr int NC = ncomp_of(DIM);
   for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < g.ncell;
        cell += (int64_t)gridDim.x * blockDim.x) {
     const Cell q = make_cell(g, cell);
@@ -100,7 +102,10 @@ static kx_status apply_t(kx_ctx* c, const void* v, void* w, int tr) {
   const int blocks = (int)std::min<int64_t>((g.ncell + NTHREADS - 1) / NTHREADS, (int64_t)c->nblk * 4);
   const T* ie = (const T*)c->d_inv_eps;
   const T* sg = (const T*)c->d_sig2;
-  if (g.dim == 2) {
+  if (g.dim == 2 && g.pml) {
+    if (tr) k_apply<T, 4, 1><<<blocks, NTHREADS, 0, c->stream>>>(g, (const T*)v, (T*)w, ie, sg);
+    else k_apply<T, 4, 0><<<blocks, NTHREADS, 0, c->stream>>>(g, (const T*)v, (T*)w, ie, sg);
+  } else if (g.dim == 2) {
     if (tr) k_apply<T, 2, 1><<<blocks, NTHREADS, 0, c->stream>>>(g, (const T*)v, (T*)w, ie, sg);
     else k_apply<T, 2, 0><<<blocks, NTHREADS, 0, c->stream>>>(g, (const T*)v, (T*)w, ie, sg);
   } else {
@@ -113,7 +118,7 @@ static kx_status apply_t(kx_ctx* c, const void* v, void* w, int tr) {
 
 // Algorithmic bytes: read v, write w, read 1/eps on the E nodes.
 kx_status launch_apply(kx_ctx* c, const void* v, void* w, int transpose) {
-  const double bytes = 2.0 * c->n * c->esize + (double)(c->geo.ncomp - c->geo.nh) * c->geo.ncell * c->esize;
+  const double bytes = 2.0 * c->n * c->esize + (double)c->geo.ne * c->geo.ncell * c->esize;
   time_begin(c);
   const kx_status st = c->d.precision == KX_FP64 ? apply_t<double>(c, v, w, transpose)
                                                  : apply_t<float>(c, v, w, transpose);
@@ -130,7 +135,7 @@ template <typename T, int DIM, int AUG, typename Mat, int TR = 0>
 __global__ void __launch_bounds__(NTHREADS) k_pass_a(Geo g, SlotSet<T> ss, int j, int64_t ld, Mat mat,
                                                     const T* __restrict__ gsrc, int ldh, int nbb, double btol) {
   pdl_enter();
-  constexpr int NC = DIM == 2 ? 3 : 6;
+  constexpr int NC = ncomp_of(DIM);
   const Slot<T> s = slot_at(ss, blockIdx.y);
   if (s.st->done || s.st->retired) return;
   __shared__ double acc[NWARPS][MMAX + 2];
@@ -442,12 +447,13 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int ns, int j, const void* gaug) 
                     ((uintptr_t)gaug % 16) == 0;
   const int64_t items = vec4 ? g.ncell / 4 : g.ncell;
   const int64_t rounds = (items + NTHREADS - 1) / NTHREADS;
-  static std::atomic<int> grid[3][2];
-  const int kind = vec4 ? 2 : (g.dim == 3);
+  static std::atomic<int> grid[4][2];
+  const int kind = vec4 ? 2 : (g.pml ? 3 : (g.dim == 3));
   std::atomic<int>& gr = grid[kind][gaug != nullptr];
   if (!gr) {
     const void* fn;
     if (vec4) fn = gaug ? (const void*)k_pass_a4<1> : (const void*)k_pass_a4<0>;
+    else if (g.dim == 2 && g.pml) fn = gaug ? (const void*)k_pass_a<T, 4, 1, TableMat<T>> : (const void*)k_pass_a<T, 4, 0, TableMat<T>>;
     else if (g.dim == 2) fn = gaug ? (const void*)k_pass_a<T, 2, 1, TableMat<T>> : (const void*)k_pass_a<T, 2, 0, TableMat<T>>;
     else fn = gaug ? (const void*)k_pass_a<T, 3, 1, TableMat<T>> : (const void*)k_pass_a<T, 3, 0, TableMat<T>>;
     gr = persistent_grid(c, fn, 1 << 30, 0);
@@ -463,6 +469,9 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int ns, int j, const void* gaug) 
     const float* sgf = (const float*)c->d_sig2;
     if (gaug) launch_k(c, k_pass_a4<1>, grd, NTHREADS, 0, c->stream, g, sf, j, c->ld, ief, sgf, (const float*)gaug, ldh, nbb, bt);
     else launch_k(c, k_pass_a4<0>, grd, NTHREADS, 0, c->stream, g, sf, j, c->ld, ief, sgf, (const float*)nullptr, ldh, nbb, bt);
+  } else if (g.dim == 2 && g.pml) {
+    if (gaug) launch_k(c, k_pass_a<T, 4, 1, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs, ldh, nbb, bt);
+    else launch_k(c, k_pass_a<T, 4, 0, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs, ldh, nbb, bt);
   } else if (g.dim == 2) {
     if (gaug) launch_k(c, k_pass_a<T, 2, 1, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs, ldh, nbb, bt);
     else launch_k(c, k_pass_a<T, 2, 0, TableMat<T>>, grd, NTHREADS, 0, c->stream, g, s, j, c->ld, TableMat<T>{ie, sg}, gs, ldh, nbb, bt);
@@ -534,7 +543,7 @@ static kx_status pass_a_tr_t(kx_ctx* c, int slot, int ns, int j) {
 
 kx_status launch_pass_a_tr(kx_ctx* c, int slot, int ns, int j) {
   const double vb = (double)c->n * c->esize;
-  const double bytes = (j + 2) * vb + (double)(c->geo.ncomp - c->geo.nh) * c->geo.ncell * c->esize;
+  const double bytes = (j + 2) * vb + (double)c->geo.ne * c->geo.ncell * c->esize;
   time_begin(c);
   const kx_status st = c->d.precision == KX_FP64 ? pass_a_tr_t<double>(c, slot, ns, j)
                                                  : pass_a_tr_t<float>(c, slot, ns, j);
@@ -551,7 +560,7 @@ kx_status launch_pass_a_cells(kx_ctx* c, int slot, int j, const double* d_eps_ce
 // vectors), write w (1), read 1/eps on the E nodes, and g when augmented.
 kx_status launch_pass_a(kx_ctx* c, int slot, int ns, int j, const void* g_aug) {
   const double vb = (double)c->n * c->esize;
-  const double bytes = (j + 2) * vb + (double)(c->geo.ncomp - c->geo.nh) * c->geo.ncell * c->esize +
+  const double bytes = (j + 2) * vb + (double)c->geo.ne * c->geo.ncell * c->esize +
                        (g_aug ? vb : 0.0);
   time_begin(c);
   const kx_status st = c->d.precision == KX_FP64 ? pass_a_t<double>(c, slot, ns, j, g_aug)
