@@ -65,6 +65,10 @@ WORKLOADS = {
                                     method="split4d", rtol=1e-11, t_oracle=60.0, batch=8, band=(1.0, 1.007)),
     "2d12_m40_T60_8f_split": dict(dim=2, n=12, ndisks=2, seed=1708, T=60.0, m=40, nfreq=8, prec="fp64",
                                   method="split", rtol=1e-11, t_oracle=60.0, batch=8, band=(1.0, 1.007)),
+    # config 1 with the paper's perfectly matched layer (auxiliary field P,
+    # quadratic sigma up to 3 over the 6-cell layers)
+    "2d64_m30_T200_pml": dict(dim=2, n=64, seed=1708, T=200.0, m=30, nfreq=1, prec="fp64",
+                              method="plain", rtol=1e-11, t_oracle=200.0, pml=True),
     # 2D 64^2, 40 disks, FP64, m = 30, T = 200, plain method
     "2d64_m30_T200": dict(dim=2, n=64, seed=1708, T=200.0, m=30, nfreq=1, prec="fp64",
                           method="plain", rtol=1e-11, t_oracle=200.0),
@@ -92,7 +96,9 @@ def shard_frequencies(nfreq, rank, world, lo=0.8, hi=1.2):
 
 def scenario_for(w, rank=0, world=1):
     import scenario as S
-    if w["dim"] == 2:
+    if w["dim"] == 2 and w.get("pml"):
+        sc = S.config_2d_pml(n=w["n"], seed=w["seed"], T=w["T"], m=w["m"], ndisks=w.get("ndisks", 40))
+    elif w["dim"] == 2:
         sc = S.config_2d(n=w["n"], seed=w["seed"], T=w["T"], m=w["m"], ndisks=w.get("ndisks", 40))
     else:
         sc = S.config_3d(n=w["n"], seed=w["seed"], fill=w["fill"], T=w["T"], m=w["m"])
@@ -191,8 +197,11 @@ def oracle_sample(w, sc):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
     one frequency's exact response over [0, t_oracle] by the augmented
     route (expm_multiply), scaled to the full interval."""
-    from oracle import exact, yee
-    op = yee.Operator(sc.grid, sc.eps_cell)
+    from oracle import exact, pml, yee
+    if getattr(sc.grid, "pml", 0):
+        op = pml.PmlOperator(sc.grid, sc.eps_cell)
+    else:
+        op = yee.Operator(sc.grid, sc.eps_cell)
     A = op.matrix()
     t_s = min(w["t_oracle"], w["T"])
     t0 = time.perf_counter()
