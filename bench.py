@@ -78,6 +78,10 @@ WORKLOADS = {
     # uneven batch: 48 instances, sizes U{32..96}^3, 4 frequencies each, concurrent
     "uneven48_4f": dict(kind="uneven", count=48, seed=1711, T=400.0, m=64, nfreq=4, prec="fp32",
                         method="plain", rtol=1e-7, threads=8),
+    # the same instances, each by restart in Krylov dimension (one basis per
+    # restart for its 4 frequencies)
+    "uneven48_4f_rst": dict(kind="uneven", count=48, seed=1711, T=400.0, m=64, nfreq=4, prec="fp32",
+                            method="rstdim", rtol=1e-7, threads=8, rst_samples=4096),
     # adjoint: 3D 96^3, 8 frequencies, gradient of the summed output-plane intensity
     "adjoint3d96_8f": dict(kind="adjoint", dim=3, n=96, seed=1712, fill=0.3, T=400.0, m=64, nfreq=8,
                            prec="fp32", method="plain", rtol=1e-7, checkpoints=128),
@@ -277,8 +281,9 @@ def run_uneven(args, w):
     dt = torch.float64 if w["prec"] == "fp64" else torch.float32
     ctxs, gs = [], []
     for sc in scs:
+        rst = w["method"] == "rstdim"
         ctxs.append(Context(sc.grid, sc.eps_cell, precision=w["prec"], krylov_dim=w["m"], max_freqs=w["nfreq"],
-                            batch=w["nfreq"], stream="own"))
+                            batch=2 if rst else w["nfreq"], stream="own", rst_samples=w.get("rst_samples", 0)))
         gs.append(torch.tensor(sc.g, dtype=dt, device="cuda"))
     torch.cuda.synchronize()
     oms = np.stack([sc.omegas for sc in scs])
@@ -288,7 +293,8 @@ def run_uneven(args, w):
     res = {}
 
     def step():
-        res["out"] = response_multi(ctxs, gs, oms, w["T"], rtol=w["rtol"], planes=planes, nthreads=w["threads"])
+        res["out"] = response_multi(ctxs, gs, oms, w["T"], rtol=w["rtol"], method=w["method"], planes=planes,
+                                    nthreads=w["threads"])
 
     dev_ms, wall, clk = timed_steps(args, dist, step, main_stream)
     launches = sum(c.stats()["kernel_launches"] for c in ctxs) - launches0
@@ -302,7 +308,8 @@ def run_uneven(args, w):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * job_s / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": args.workload, "instances": len(scs), "sizes_min_max": [min(sizes), max(sizes)],
+                "config": {"workload": args.workload, "method": w["method"], "instances": len(scs),
+                           "sizes_min_max": [min(sizes), max(sizes)],
                            "unknowns_total": int(sum(sc.grid.nunk for sc in scs)), "nfreq_each": w["nfreq"],
                            "T": w["T"], "krylov_dim": w["m"], "host_threads": w["threads"],
                            "timing": "wall clock around the synchronised multi-problem call",
