@@ -53,7 +53,7 @@ WORKLOADS = {
                                   prec="fp32", method="rstdim", rtol=1e-7, t_oracle=20.0, rst_samples=4096,
                                   batch=2),
     "3d128_32f_T400_rst": dict(dim=3, n=128, seed=1710, fill=0.3, T=400.0, m=64, nfreq=32,
-                               prec="fp32", method="rstdim", rtol=1e-7, t_oracle=4.0, rst_samples=4096,
+                               prec="fp32", method="rstdim", rtol=1e-7, t_oracle=0.5, rst_samples=4096,
                                batch=2),
     # source splitting (eq. (split2)) on the 64^3 medium, 32 frequencies in lockstep
     "3d64_m64_T400_32f_split2": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=32,
@@ -86,7 +86,7 @@ WORKLOADS = {
     "adjoint3d96_8f": dict(kind="adjoint", dim=3, n=96, seed=1712, fill=0.3, T=400.0, m=64, nfreq=8,
                            prec="fp32", method="plain", rtol=1e-7, checkpoints=128),
 }
-DEFAULT = "3d64_m64_T400_32f_rst"
+DEFAULT = "3d128_32f_T400_rst"
 
 
 def shard_frequencies(nfreq, rank, world, lo=0.8, hi=1.2):
