@@ -31,9 +31,10 @@ sys.path.insert(0, ROOT)
 METRIC = "freq responses/s at 1e-6 rel err vs per-freq Krylov; A·v+GS HBM GB/s"
 
 # DRAM bytes / algorithmic bytes per launch of the two Arnoldi kernels, from
-# the ncu captures summarised in profiles/rstdim_3d64_32f_ncu.md (single
-# basis, steps j = 60, 61).  Set to None whenever those kernels change.
-NCU_TRAFFIC_RATIO = {"k_pass_a": 1.012, "k_pass_b": 1.000}
+# the ncu captures summarised in profiles/rstdim_3d128_32f_ncu.md (single
+# basis, step j = 60, 96^3; the ratio carries over to other sizes).  Set to
+# None whenever those kernels change.
+NCU_TRAFFIC_RATIO = {"k_pass_a": 1.014, "k_pass_b": 1.000}
 
 WORKLOADS = {
     # 3D Yee 64^3, random eps=2.25 spheres (fill 0.3, r 2-5), 8-cell layer,
@@ -52,6 +53,9 @@ WORKLOADS = {
     "3d64_m64_T400_32f_rst": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=32,
                                   prec="fp32", method="rstdim", rtol=1e-7, t_oracle=20.0, rst_samples=4096,
                                   batch=2),
+    "3d96_32f_T400_rst": dict(dim=3, n=96, seed=1713, fill=0.3, T=400.0, m=64, nfreq=32,
+                              prec="fp32", method="rstdim", rtol=1e-7, t_oracle=1.0, rst_samples=4096,
+                              batch=2),
     "3d128_32f_T400_rst": dict(dim=3, n=128, seed=1710, fill=0.3, T=400.0, m=64, nfreq=32,
                                prec="fp32", method="rstdim", rtol=1e-7, t_oracle=0.5, rst_samples=4096,
                                batch=2),
