@@ -469,9 +469,9 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int ns, int j, const void* gaug) 
                     ((uintptr_t)gaug % 16) == 0;
   const int64_t items = vec4 ? g.ncell / 4 : g.ncell;
   const int64_t rounds = (items + NTHREADS - 1) / NTHREADS;
-  // the quad kernel in its three-block form when the work exceeds what two
-  // resident blocks per SM cover
-  const bool dense = vec4 && rounds > 2 * (int64_t)c->nsm;
+  // the quad kernel in its three-block form when the launch's work (all its
+  // slots) exceeds what two resident blocks per SM cover
+  const bool dense = vec4 && rounds * ns > 2 * (int64_t)c->nsm;
   static std::atomic<int> grid[5][2];
   const int kind = vec4 ? (dense ? 4 : 2) : (g.pml ? 3 : (g.dim == 3));
   std::atomic<int>& gr = grid[kind][gaug != nullptr];
