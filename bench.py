@@ -409,6 +409,7 @@ def main():
     clocks = Clocks()
     clocks.start()
     launches0 = ctx.stats()["kernel_launches"]
+    steps0 = ctx.stats()["arnoldi_steps"]
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -424,6 +425,7 @@ def main():
     clk = clocks.stop(local)
     dev_ms = ev0.elapsed_time(ev1)
     launches = ctx.stats()["kernel_launches"] - launches0
+    krylov_steps = ctx.stats()["arnoldi_steps"] - steps0
     dev_ms = barrier_max(dist, dev_ms)
     ms_per_step = dev_ms / args.steps
     responses = w["nfreq"] * args.steps * world
@@ -529,6 +531,7 @@ def main():
                            "l2": "working set (Krylov basis) larger than L2; no flush"},
                 "roofline": roofline,
                 "arnoldi_hbm_gbs": round(ab_gbs, 1),
+                "krylov_steps_per_s": round(krylov_steps * world / (dev_ms / 1000.0), 1),
                 "kernel_ms_per_step": {k: round(v["ms"], 3) for k, v in kt.items()},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                 "accuracy": acc,
