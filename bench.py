@@ -453,13 +453,14 @@ def main():
     kt = ctx.kernel_times()
     ctx.set_timing(False)
     total_ms = sum(v["ms"] for v in kt.values())
-    dom = max(("pass_a", "pass_b"), key=lambda k: kt[k]["ms"])
+    dom = max(("pass_a", "pass_b", "sweep"), key=lambda k: kt[k]["ms"])
     peak, peak_kind = peaks()
     ach = kt[dom]["bytes"] / (kt[dom]["ms"] / 1000.0) / 1e9 if kt[dom]["ms"] > 0 else 0.0
-    ab_bytes = kt["pass_a"]["bytes"] + kt["pass_b"]["bytes"]
-    ab_ms = kt["pass_a"]["ms"] + kt["pass_b"]["ms"]
+    arn = ("pass_a", "pass_b", "sweep", "swapply")      # every kernel of the Arnoldi process
+    ab_bytes = sum(kt[k]["bytes"] for k in arn)
+    ab_ms = sum(kt[k]["ms"] for k in arn)
     ab_gbs = ab_bytes / (ab_ms / 1000.0) / 1e9 if ab_ms > 0 else 0.0
-    kname = f"k_pass_{dom[-1]}"
+    kname = {"pass_a": "k_pass_a", "pass_b": "k_pass_b", "sweep": "k_sw_pass"}[dom]
     avg_bytes = kt[dom]["bytes"] / max(1, kt[dom]["launches"])
     ratio = NCU_TRAFFIC_RATIO.get(kname)
     roofline = {"bound": "hbm", "kernel": kname, "achieved": round(ach, 1),

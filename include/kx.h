@@ -52,6 +52,21 @@ typedef enum {
 enum { KX_PERIODIC = 0, KX_PEC = 1 };
 enum { KX_FP64 = 0, KX_FP32 = 1 };
 enum { KX_PLAIN = 0, KX_SPLIT = 1, KX_RSTDIM = 2, KX_SPLIT2 = 3, KX_SPLIT4D = 4 };
+/* Form of the Arnoldi process (kx_desc.arnoldi_form).  Both are classical
+ * Gram-Schmidt (Sect. 3.2, eq. (Arn)) and agree up to rounding.
+ *   KX_ARN_DEFAULT: the single-sweep form for restart in Krylov dimension,
+ *                   the two-pass form everywhere else.
+ *   KX_ARN_TWOPASS: per step, one pass applies A fused with the dots
+ *                   V_j^T A v_j, a second applies the update and the norm;
+ *                   the basis is read twice.
+ *   KX_ARN_SWEEP:   per step, one pass reads the basis once: it forms the new
+ *                   column from the explicit A v_{j-1} and, from A^2 v_{j-1},
+ *                   the dots that give the next Hessenberg column through
+ *                   the Arnoldi relation and the Gram matrix of the basis.
+ *                   A second, light pass applies A to the new column.  Used
+ *                   wherever the process carries no augmented source phase:
+ *                   restart in Krylov dimension and arnoldi(). */
+enum { KX_ARN_DEFAULT = 0, KX_ARN_TWOPASS = 1, KX_ARN_SWEEP = 2 };
 
 /* Problem descriptor.  Grid of n[0] x n[1] (x n[2]) unit cells; the
  * absorbing layer (conductivity ramping linearly from 0 to sigma_max over
@@ -84,6 +99,8 @@ typedef struct {
                          sigma = sigma_max (d/L)^2 damping Hy and Ez only.
                          n = 4 ncell; the output plane holds Ez; the adjoint
                          and kx_arnoldi_noalloc reject it                    */
+  int arnoldi_form;   /* KX_ARN_DEFAULT, KX_ARN_TWOPASS or KX_ARN_SWEEP (above);
+                         kx_arnoldi_noalloc always runs the two-pass form   */
 } kx_desc;
 
 typedef struct kx_ctx kx_ctx;
@@ -129,7 +146,9 @@ kx_status apply_A(kx_ctx* ctx, const void* d_v, void* d_w, int transpose);
 
 /* m steps of the Arnoldi process for K_m(A, v0) (Sect. 3.2, eqs. (Arn),
  * (Arn1)): A V_m = V_{m+1} H, v_1 = v0/||v0||.  Classical Gram-Schmidt,
- * dots fused with the operator application.
+ * dots fused with the operator application; the descriptor's arnoldi_form
+ * picks the two-pass form (KX_ARN_DEFAULT, KX_ARN_TWOPASS) or the
+ * single-sweep form (KX_ARN_SWEEP).
  *   d_v0  : device, n scalars (not modified).
  *   m     : 1 .. krylov_dim.
  *   d_V   : device n x (m+1) column-major (leading dim n) receiving the
@@ -310,7 +329,9 @@ enum { KX_K_PASS_A = 0,    /* operator application fused with the Gram-Schmidt d
        KX_K_ZUPDATE = 4,   /* multi-shift update of the stationary parts            */
        KX_K_APPLY = 5,     /* plain operator application                            */
        KX_K_CASCADE = 6,   /* projected time stepping of restart in dimension       */
-       KX_NKCLASS = 7 };
+       KX_K_SWEEP = 7,     /* single-sweep Arnoldi: update, dots and norms in one pass */
+       KX_K_SWAPPLY = 8,   /* single-sweep Arnoldi: A applied to the new column     */
+       KX_NKCLASS = 9 };
 typedef struct {
   double ms;
   double bytes;
@@ -345,7 +366,9 @@ const char* kx_last_error(const kx_ctx* ctx);
  *               otherwise); returned orthonormal as by arnoldi().
  *   d_H       : device (m+1) x m FP64 Hessenberg matrix (column-major).
  *   beta, m_done: host outputs as for arnoldi().
- * Results match arnoldi() on a context with the same descriptor.  The call
+ * Results match arnoldi() on a context with the same descriptor and
+ * arnoldi_form KX_ARN_DEFAULT or KX_ARN_TWOPASS (this entry runs the
+ * two-pass form whatever the descriptor's arnoldi_form).  The call
  * synchronises cuda_stream.  Its first call on a device takes the device
  * address of the scratch array (set-up), so make that first call before any
  * stream capture.  All calls share the array and it keeps the last call's

@@ -30,7 +30,9 @@ EXPORTS = ["krylov_expm_create", "krylov_expm_destroy", "kx_num_unknowns", "appl
            "kx_kernel_times", "kx_last_error", "kx_arnoldi_noalloc", "kx_noalloc_last_error",
            "adjoint_response_grad", "kx_set_permittivity", "response_at_freqs_multi", "kx_stream",
            "response_restart_dim"]
-KCLASSES = ["pass_a", "pass_b", "restart", "projected", "zupdate", "apply", "cascade"]
+KCLASSES = ["pass_a", "pass_b", "restart", "projected", "zupdate", "apply", "cascade", "sweep", "swapply"]
+# Arnoldi forms (kx_desc.arnoldi_form)
+ARNOLDI_FORMS = {"default": 0, "twopass": 1, "sweep": 2}
 
 
 class KxError(RuntimeError):
@@ -44,7 +46,8 @@ class Desc(ctypes.Structure):
                 ("layer_axis", ctypes.c_int), ("layer_cells", ctypes.c_int),
                 ("sigma_max", ctypes.c_double), ("precision", ctypes.c_int),
                 ("krylov_dim", ctypes.c_int), ("max_freqs", ctypes.c_int), ("batch", ctypes.c_int),
-                ("max_checkpoints", ctypes.c_int), ("rst_samples", ctypes.c_int), ("pml", ctypes.c_int)]
+                ("max_checkpoints", ctypes.c_int), ("rst_samples", ctypes.c_int), ("pml", ctypes.c_int),
+                ("arnoldi_form", ctypes.c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -125,11 +128,13 @@ class Context:
     problems, since torch hands out streams from a small pool).
     ``rst_samples``: time samples per frequency held for the restart-in-
     dimension method (``method="rstdim"``; 0 leaves it unavailable).
+    ``arnoldi``: "default" (single sweep for restart in dimension, two passes
+    elsewhere), "twopass" or "sweep" (also for ``arnoldi()``).
     """
 
     def __init__(self, grid, eps_cell, precision: str = "fp32", krylov_dim: int = 64,
                  max_freqs: int = 1, batch: int = 1, stream=None, max_checkpoints: int = 0,
-                 rst_samples: int = 0):
+                 rst_samples: int = 0, arnoldi: str = "default"):
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -150,6 +155,9 @@ class Context:
         d.max_checkpoints = max_checkpoints
         d.rst_samples = rst_samples
         d.pml = int(getattr(grid, "pml", 0))
+        if arnoldi not in ARNOLDI_FORMS:
+            raise ValueError(f"arnoldi must be one of {sorted(ARNOLDI_FORMS)}")
+        d.arnoldi_form = ARNOLDI_FORMS[arnoldi]
         self.desc = d
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         own = isinstance(stream, str) and stream == "own"

@@ -406,6 +406,8 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
   if (d.pml && (d.dim != 2 || d.layer_axis != 0))
     return fail(nullptr, KX_EINVAL, "the PML model is 2D with the layer along x (layer_axis 0)");
   if (d.pml && d.max_checkpoints > 0) return fail(nullptr, KX_EINVAL, "the adjoint does not cover the PML model");
+  if (d.arnoldi_form != KX_ARN_DEFAULT && d.arnoldi_form != KX_ARN_TWOPASS && d.arnoldi_form != KX_ARN_SWEEP)
+    return fail(nullptr, KX_EINVAL, "arnoldi_form must be KX_ARN_DEFAULT, KX_ARN_TWOPASS or KX_ARN_SWEEP");
   const int nz = d.dim == 3 ? d.n[2] : 1;
   const int64_t ncell = (int64_t)d.n[0] * d.n[1] * nz;
   for (int64_t i = 0; i < ncell; ++i)
@@ -489,6 +491,10 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
       {(void**)&c->d_expm_ws, (size_t)(MMAX + 1) * MMAX * MAXF * sizeof(double)},
       {(void**)&c->d_zre, (size_t)d.max_freqs * c->n * c->esize},
       {(void**)&c->d_zim, (size_t)d.max_freqs * c->n * c->esize},
+      {(void**)&c->d_swT, (size_t)c->n * c->esize},
+      {(void**)&c->d_swpart, (size_t)B * SWCOLS * c->ps * sizeof(double)},
+      {(void**)&c->d_swG, (size_t)B * (MMAX + 1) * (MMAX + 1) * sizeof(double)},
+      {(void**)&c->d_swco, (size_t)B * sizeof(SwCoef)},
   };
   for (auto& a : allocs) {
     e = cudaMalloc(a.p, a.bytes);
@@ -570,6 +576,7 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
     return fail(nullptr, KX_ENOMEM, "pinned host allocation failed");
   }
   e = cudaMemsetAsync(c->d_counter, 0, (size_t)B * 8 * sizeof(unsigned), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_swco, 0, (size_t)B * sizeof(SwCoef), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_state, 0, (size_t)B * sizeof(SlotState), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_V, 0, bytes_V, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_aug, 0, (size_t)B * (m + 1) * 2 * sizeof(double), c->stream);
@@ -603,7 +610,7 @@ kx_status krylov_expm_destroy(kx_ctx* c) {
                   c->d_omegas, c->d_small, c->d_tmp, c->d_tmp2, c->d_expm_ws, c->d_zre, c->d_zim,
                   c->d_ckpt, c->d_adj_Q, c->d_adj_alpha, c->d_adj_omg, c->d_adj_cw, c->d_adj_sn,
                   c->d_gauss, c->d_rst_b, c->d_rst_smp, c->d_rst_mats, c->d_rst_u, c->d_rst_res,
-                  c->d_rst_state, c->d_rst_yp};
+                  c->d_rst_state, c->d_rst_yp, c->d_swT, c->d_swpart, c->d_swG, c->d_swco};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_state) cudaFreeHost(c->h_state);
@@ -648,7 +655,8 @@ kx_status arnoldi(kx_ctx* c, const void* d_v0, int m, void* d_V, double* H, doub
   SlotState st;
   KX_TRY(read_state(c, slot, &st));
   if (!(st.beta > 0.0) || !std::isfinite(st.beta)) return fail(c, KX_ENONFINITE, "v0 is zero or non-finite");
-  KX_TRY(arnoldi_steps(c, slot, 1, m, nullptr));
+  if (c->d.arnoldi_form == KX_ARN_SWEEP) KX_TRY(sweep_arnoldi(c, slot, m));
+  else KX_TRY(arnoldi_steps(c, slot, 1, m, nullptr));
   KX_TRY(read_state(c, slot, &st));
   if (st.status) return fail(c, (kx_status)st.status, "non-finite value in the Arnoldi process");
   *beta = st.beta;
@@ -883,6 +891,14 @@ kx_status response_at_freqs(kx_ctx* c, const void* d_g, const double* omegas, in
   return KX_OK;
 }
 
+// The Arnoldi process of one restart in Krylov dimension (basis slot
+// `slot`, non-augmented): the single-sweep form unless the descriptor asks
+// for the two-pass form.
+kx_status rst_arnoldi(kx_ctx* c, int slot) {
+  if (c->d.arnoldi_form == KX_ARN_TWOPASS) return arnoldi_steps(c, slot, 1, c->m, nullptr);
+  return sweep_arnoldi(c, slot, c->m);
+}
+
 kx_status response_restart_dim(kx_ctx* c, const void* d_g, const double* omegas, int nfreq, double T,
                                double rtol, double dt_sample, int max_restarts, const int* plane,
                                void* d_E_plane, double* intensity, double* resid, int* restarts, void* d_Y) {
@@ -948,7 +964,7 @@ kx_status response_restart_dim(kx_ctx* c, const void* d_g, const double* omegas,
   }
   KX_CUDA(c, cudaMemcpyAsync(c->d_omegas, omegas, sizeof(double) * nfreq, cudaMemcpyHostToDevice, A),
           "omega upload");
-  KX_TRY(arnoldi_steps(c, 0, 1, c->m, nullptr));
+  KX_TRY(rst_arnoldi(c, 0));
   KX_TRY(read_state(c, 0, &st));
   if (st.status) return fail(c, (kx_status)st.status, "non-finite value in the Arnoldi process");
   // sample grid from ||H_m||_1 of the first restart
@@ -1004,7 +1020,7 @@ kx_status response_restart_dim(kx_ctx* c, const void* d_g, const double* omegas,
         if (k >= 2) KX_CUDA(c, cudaStreamWaitEvent(A, c->ev_proj[nx], 0), "event wait");
         KX_TRY(launch_rst_nextvec(c, A, sl, nx));
         KX_TRY(launch_norm_init(c, nx, 1));
-        KX_TRY(arnoldi_steps(c, nx, 1, c->m, nullptr));
+        KX_TRY(rst_arnoldi(c, nx));
         KX_CUDA(c, cudaEventRecord(c->ev_arnoldi, A), "event record");
       }
     }
@@ -1031,7 +1047,7 @@ kx_status response_restart_dim(kx_ctx* c, const void* d_g, const double* omegas,
       // the next basis starts from v_{m+1} (same slot, column m_done -> 0)
       KX_TRY(launch_rst_nextvec(c, A, 0, 0));
       KX_TRY(launch_norm_init(c, 0, 1));
-      KX_TRY(arnoldi_steps(c, 0, 1, c->m, nullptr));
+      KX_TRY(rst_arnoldi(c, 0));
     }
   }
   if (ovl) KX_CUDA(c, cudaStreamWaitEvent(A, c->ev_proj[0], 0), "event wait");

@@ -127,6 +127,29 @@ constexpr int RST_OFF_R2 = RST_OFF_R1 + MMAX;
 constexpr int RST_OFF_SC = RST_OFF_R2 + MMAX;
 constexpr int RST_MATS = RST_OFF_SC + 8;
 
+// Single-sweep Arnoldi (sweep.cu): reduced partial columns of the last
+// pass, and the coefficients the next sweep applies.  One record per slot.
+constexpr int SWCOLS = 2 * MMAX + 3;   // dots against t2 and t1 per column, x.x, x.y, y.y
+struct SwCoef {
+  double tot[SWCOLS];   // reduced columns of the last sweep (step 0: v_0 . A v_0, ||A v_0||^2)
+  double hc[MMAX + 1];  // h_{i,j-1}, i < j: the column the sweep S_j removes from A v_{j-1}
+  double cp[MMAX + 1];  // c_k, k < j: sum_{i<j-1} h_{k,i} h_{i,j-1} (A v_i through the Arnoldi relation)
+  double uh[MMAX + 1];  // sum_{l=i}^{j-1} G_{i,l} hc_l, row i < j (apply pass K_j)
+  double uc[MMAX + 1];  // sum_{k=i}^{j-1} G_{i,k} c_k,  row i < j (apply pass K_j)
+  double sprev;         // scale of column j-1
+  double hjj;           // h_{j-1,j-1}
+  unsigned counter;     // block-completion counter of the apply pass
+};
+
+// Pointers of the single-sweep workspace of one slot.
+struct SwSlot {
+  double* part;   // SWCOLS x ps block partials, column-major by block
+  int ps;
+  double* G;      // (MMAX+1) x (MMAX+1) Gram matrix v_i . v_k, column-major
+  SwCoef* co;
+  void* t;        // one vector: A V_{j-1} (shared by the slots: one process runs at a time)
+};
+
 struct Material {
   const void* inv_eps;   // (ncomp - nh) x ncell, 1 / mean eps on E nodes
   const void* sig2;      // sigma at 2*index + half along the layer axis
@@ -192,6 +215,11 @@ struct kx_ctx {
   cudaStream_t aux_stream = nullptr;   // projected work overlapping the next Arnoldi process
   int side_ctas = 0;        // long-lived CTAs of other kernels sharing the SMs meanwhile
   int pdl = 0;              // launch the Arnoldi chain with programmatic dependent launch
+  // single-sweep Arnoldi workspace (per slot, and one shared vector)
+  void* d_swT = nullptr;
+  double* d_swpart = nullptr;
+  double* d_swG = nullptr;
+  kx::SwCoef* d_swco = nullptr;
   cudaEvent_t ev_arnoldi = nullptr;    // Arnoldi process of a restart complete
   cudaEvent_t ev_proj[2] = {nullptr, nullptr};  // projected work done with basis slot 0 / 1
   kx_stats stats;
@@ -254,6 +282,10 @@ kx_status launch_rst_out(kx_ctx* c, cudaStream_t st, int nfreq, int64_t P, void*
                          void* Y);
 // column m_done of basis slot `from` (the unnormalised v_{m+1}) -> column 0 of slot `to`
 kx_status launch_rst_nextvec(kx_ctx* c, cudaStream_t st, int from, int to);
+
+// sweep.cu: m steps of the single-sweep Arnoldi process on basis slot
+// `slot`, from its column 0 as set by launch_norm_init (non-augmented)
+kx_status sweep_arnoldi(kx_ctx* c, int slot, int m);
 
 // projected.cu
 kx_status launch_substep_control(kx_ctx* c, int slot0, int ns);

@@ -214,4 +214,104 @@ __device__ __forceinline__ void stencil(const Geo& g, const T* __restrict__ v, c
 }
 
 
+// ---------------------------------------------------------------------------
+// The 3D lossy-layer model in FP32 on four consecutive x-cells (a quad;
+// nx % 4 == 0): every field and 1/eps access is one 16-byte load, the
+// x-neighbours of the quad's end cells are one scalar each.
+__device__ __forceinline__ float4 ld4(const float* __restrict__ p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float f4(const float4& v, int e) { return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w)); }
+__device__ __forceinline__ void set4(float4& v, int e, float x) {
+  if (e == 0) v.x = x; else if (e == 1) v.y = x; else if (e == 2) v.z = x; else v.w = x;
+}
+__device__ __forceinline__ float dot4(const float4& a, const float4& b) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+// zero the elements of a quad that lie on a wall of component c
+__device__ __forceinline__ float4 wall4(const Geo& g, int c, float4 v, int i0, int j, int k) {
+  const unsigned mb = g.maskbits[c];
+  if (((mb & 2u) && j == 0) || ((mb & 4u) && k == 0)) return make_float4(0.f, 0.f, 0.f, 0.f);
+  if ((mb & 1u) && i0 == 0) v.x = 0.f;
+  return v;
+}
+__device__ __forceinline__ float wall1(const Geo& g, int c, float v, int i, int j, int k) {
+  return is_wall(g, c, i, j, k) ? 0.f : v;
+}
+
+struct Quad {
+  int64_t c0;      // first cell
+  int i0, jj, kk;  // its indices
+};
+
+__device__ __forceinline__ Quad make_quad(const Geo& g, int64_t q4) {
+  Quad q;
+  q.c0 = q4 << 2;
+  q.i0 = (int)(q.c0 % g.nx);
+  const int64_t r = q.c0 / g.nx;
+  q.jj = (int)(r % g.ny);
+  q.kk = (int)(r / g.ny);
+  return q;
+}
+
+// out[c] = component c of A v on the quad's four cells (wall nodes zero);
+// the rows of eq. (ode) as in stencil<float, 3, 0, TableMat<float>>.
+__device__ __forceinline__ void stencil_quad(const Geo& g, const float* __restrict__ v, const float* __restrict__ ie,
+                                             const float* __restrict__ sig2, const Quad& q, float4 out[6]) {
+  const int64_t nc = g.ncell;
+  const int64_t nxy = (int64_t)g.nx * g.ny;
+  const int64_t c0 = q.c0;
+  const int i0 = q.i0, jj = q.jj, kk = q.kk;
+  const int jp = (jj + 1 == g.ny) ? 0 : jj + 1, jm = (jj == 0) ? g.ny - 1 : jj - 1;
+  const int kp = (kk + 1 == g.nz) ? 0 : kk + 1, km = (kk == 0) ? g.nz - 1 : kk - 1;
+  const int64_t cjp = c0 + (int64_t)(jp - jj) * g.nx, cjm = c0 + (int64_t)(jm - jj) * g.nx;
+  const int64_t ckp = c0 + (int64_t)(kp - kk) * nxy, ckm = c0 + (int64_t)(km - kk) * nxy;
+  const int ixp = (i0 + 4 == g.nx) ? 0 : i0 + 4;     // first element of the next quad
+  const int ixm = (i0 == 0) ? g.nx - 1 : i0 - 1;     // element before the quad
+  const int64_t cxp = c0 - i0 + ixp, cxm = c0 - i0 + ixm;
+  const float4 Hx = wall4(g, 0, ld4(v + c0), i0, jj, kk);
+  const float4 Hy = wall4(g, 1, ld4(v + nc + c0), i0, jj, kk);
+  const float4 Hz = wall4(g, 2, ld4(v + 2 * nc + c0), i0, jj, kk);
+  const float4 Ex = wall4(g, 3, ld4(v + 3 * nc + c0), i0, jj, kk);
+  const float4 Ey = wall4(g, 4, ld4(v + 4 * nc + c0), i0, jj, kk);
+  const float4 Ez = wall4(g, 5, ld4(v + 5 * nc + c0), i0, jj, kk);
+  const float4 Ez_jp = wall4(g, 5, ld4(v + 5 * nc + cjp), i0, jp, kk);
+  const float4 Ex_jp = wall4(g, 3, ld4(v + 3 * nc + cjp), i0, jp, kk);
+  const float4 Ey_kp = wall4(g, 4, ld4(v + 4 * nc + ckp), i0, jj, kp);
+  const float4 Ex_kp = wall4(g, 3, ld4(v + 3 * nc + ckp), i0, jj, kp);
+  const float4 Hz_jm = wall4(g, 2, ld4(v + 2 * nc + cjm), i0, jm, kk);
+  const float4 Hx_jm = wall4(g, 0, ld4(v + cjm), i0, jm, kk);
+  const float4 Hy_km = wall4(g, 1, ld4(v + nc + ckm), i0, jj, km);
+  const float4 Hx_km = wall4(g, 0, ld4(v + ckm), i0, jj, km);
+  const float Ez_n = wall1(g, 5, v[5 * nc + cxp], ixp, jj, kk);
+  const float Ey_n = wall1(g, 4, v[4 * nc + cxp], ixp, jj, kk);
+  const float Hz_p = wall1(g, 2, v[2 * nc + cxm], ixm, jj, kk);
+  const float Hy_p = wall1(g, 1, v[nc + cxm], ixm, jj, kk);
+  const float4 ie0 = ld4(ie + c0), ie1 = ld4(ie + nc + c0), ie2 = ld4(ie + 2 * nc + c0);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int i = i0 + e;
+    const int li = g.la == 0 ? i : (g.la == 1 ? jj : kk);
+    float sg[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sg[c] = sig2[2 * li + g.sighalf[c]];
+    const float ez = f4(Ez, e), ey = f4(Ey, e), ex = f4(Ex, e);
+    const float hx = f4(Hx, e), hy = f4(Hy, e), hz = f4(Hz, e);
+    const float ez_ip = e < 3 ? f4(Ez, e + 1) : Ez_n;
+    const float ey_ip = e < 3 ? f4(Ey, e + 1) : Ey_n;
+    const float hz_im = e > 0 ? f4(Hz, e - 1) : Hz_p;
+    const float hy_im = e > 0 ? f4(Hy, e - 1) : Hy_p;
+    const float cHx = (hz - f4(Hz_jm, e)) - (hy - f4(Hy_km, e));
+    const float cHy = (hx - f4(Hx_km, e)) - (hz - hz_im);
+    const float cHz = (hy - hy_im) - (hx - f4(Hx_jm, e));
+    float o[6];
+    o[0] = sg[0] * hx + ((f4(Ez_jp, e) - ez) - (f4(Ey_kp, e) - ey));
+    o[1] = sg[1] * hy + ((f4(Ex_kp, e) - ex) - (ez_ip - ez));
+    o[2] = sg[2] * hz + ((ey_ip - ey) - (f4(Ex_jp, e) - ex));
+    o[3] = f4(ie0, e) * (sg[3] * ex - cHx);
+    o[4] = f4(ie1, e) * (sg[4] * ey - cHy);
+    o[5] = f4(ie2, e) * (sg[5] * ez - cHz);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) set4(out[c], e, is_wall(g, c, i, jj, kk) ? 0.f : o[c]);
+  }
+}
+
 }  // namespace kx

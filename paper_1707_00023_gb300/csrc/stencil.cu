@@ -215,26 +215,10 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_a(Geo g, SlotSet<T> ss, int j
 
 // ---------------------------------------------------------------------------
 // Pass A, 3D FP32, four consecutive x-cells per thread (nx % 4 == 0): every
-// field, 1/eps and basis access is one 16-byte load, and the dots of a chunk
-// of 8 basis columns keep 48 such loads in flight per thread.
-__device__ __forceinline__ float4 ld4(const float* __restrict__ p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ float f4(const float4& v, int e) { return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w)); }
-__device__ __forceinline__ void set4(float4& v, int e, float x) {
-  if (e == 0) v.x = x; else if (e == 1) v.y = x; else if (e == 2) v.z = x; else v.w = x;
-}
-__device__ __forceinline__ float dot4(const float4& a, const float4& b) {
-  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
-}
-// zero the elements of a quad that lie on a wall of component c
-__device__ __forceinline__ float4 wall4(const Geo& g, int c, float4 v, int i0, int j, int k) {
-  const unsigned mb = g.maskbits[c];
-  if (((mb & 2u) && j == 0) || ((mb & 4u) && k == 0)) return make_float4(0.f, 0.f, 0.f, 0.f);
-  if ((mb & 1u) && i0 == 0) v.x = 0.f;
-  return v;
-}
-__device__ __forceinline__ float wall1(const Geo& g, int c, float v, int i, int j, int k) {
-  return is_wall(g, c, i, j, k) ? 0.f : v;
-}
+// field, 1/eps and basis access is one 16-byte load (helpers in
+// kx_stencil.cuh), and the dots of a chunk of 8 basis columns keep 48 such
+// loads in flight per thread.  The stencil is written out here rather than
+// through stencil_quad: interleaved with the scaling it needs fewer registers.
 
 // The body of pass A in its quad form; two kernels below instantiate it.
 template <int AUG>

@@ -1,0 +1,677 @@
+// Single-sweep Arnoldi process (Sect. 3.2, eqs. (Arn), (Arn1)): classical
+// Gram-Schmidt arranged so that one pass over the stored basis per step
+// both builds the new column and yields the dots of the next Hessenberg
+// column.  The two-pass form (stencil.cu / linalg.cu) reads the basis twice
+// per step, once for the dots and once for the update.
+//
+// Notation: stored columns V_i with scales s_i (v_i = s_i V_i, delayed
+// normalisation as in the two-pass form); h_{i,j} the Hessenberg entries,
+// beta_j = h_{j+1,j}.  Step j >= 1 takes two launches:
+//   apply K_{j-1}: t = A V_{j-1}                       (one vector written)
+//   sweep S_j    : t1 = s_{j-1} t = A v_{j-1},  t2 = A t1 = A^2 v_{j-1},
+//                  x  = t1 - sum_{i<j} h_{i,j-1} v_i   (= beta_{j-1} v_j, stored as V_j)
+//                  y  = A x = t2 - h_{j-1,j-1} t1 - sum_{k<j} c_k v_k,
+// where the Arnoldi relation A v_i = sum_{k<=i+1} h_{k,i} v_k (i < j-1)
+// gives c = H(0:j, 0:j-1) h(0:j-1, j-1).  The sweep removes the columns from
+// x and y in the order i = 0 .. j-1 and, just before removing column i,
+// takes the explicit dots b'_i = V_i . x^(i), a'_i = V_i . y^(i) with the
+// partly reduced vectors x^(i) = t1 - sum_{k<i} h_{k,j-1} v_k (y^(i) alike);
+// with the Gram matrix G_{i,k} = v_i . v_k these give
+//   beta_{j-1} = ||x||,   v_j = x / beta_{j-1},
+//   G_{i,j} = v_i . v_j   = (s_i b'_i - sum_{l=i}^{j-1} G_{i,l} h_{l,j-1}) / beta_{j-1},
+//   h_{i,j} = v_i . A v_j = (s_i a'_i - sum_{k=i}^{j-1} G_{i,k} c_k) / beta_{j-1}   (i < j),
+//   h_{j,j} = x.y / x.x,
+// so Hessenberg column j is known when the sweep ends and only two vectors
+// (x, y) stay live per cell.  Every vector that enters a column is an
+// explicit product with the stored basis (A v_{j-1} is recomputed from
+// V_{j-1}, never carried from step to step), so rounding does not
+// accumulate through the relation; G carries the measured loss of
+// orthogonality into the derived dots.  In exact arithmetic the process is
+// classical Gram-Schmidt.
+//
+// Bytes per step (n unknowns, s bytes a scalar): the apply pass reads V_{j-1}
+// and writes t (2 n s), the sweep reads t and V_0..V_{j-1} and writes V_j
+// ((j + 2) n s), plus the 1/eps table in each: about (j + 5) n s against
+// (2 j + 5) n s for the two-pass form.
+#include <atomic>
+
+#include "kx_internal.cuh"
+#include "kx_reduce.cuh"
+#include "kx_stencil.cuh"
+
+namespace kx {
+
+namespace {
+
+constexpr int LG = MMAX + 1;   // leading dimension of the Gram matrix
+
+// Sum over the four lanes of a row group (lanes 4r .. 4r+3) in a fixed order.
+__device__ __forceinline__ double quad_sum(double x) {
+  x += __shfl_xor_sync(0xffffffffu, x, 1);
+  x += __shfl_xor_sync(0xffffffffu, x, 2);
+  return x;
+}
+
+// Finalisation of step j, run by one whole block.
+//   j == 0: tot = [V_0 . A V_0, ||A V_0||^2] (unscaled): h_{0,0}, ||A v_0||.
+//   j >= 1: tot = sweep S_j's columns [a'_0..a'_{j-1}, b'_0..b'_{j-1}, x.x,
+//           x.y, y.y] and uh, uc the row products of apply pass K_j:
+//           beta_{j-1}, scale_j, m_done = j, the breakdown test, then
+//           (unless final_step or the process stopped) G column j, H column
+//           j and the coefficients of sweep S_{j+1}.
+// tot, uh and uc were written by other blocks of the same launch: read past L1.
+template <typename T>
+__device__ void sw_fin(const Slot<T>& s, SwCoef* co, double* G, int j, int ldh, double btol, int final_step) {
+  __shared__ double sh_h[MMAX + 1];
+  __shared__ double sh_beta, sh_sig;
+  __shared__ int sh_stop;
+  SlotState* st = s.st;
+  const int tid = threadIdx.x;
+  if (j == 0) {
+    if (tid == 0) {
+      const double s0 = s.scale[0];
+      const double h00 = s0 * s0 * __ldcg(&co->tot[0]);
+      const double an = s0 * sqrt(__ldcg(&co->tot[1]));
+      s.H[0] = h00;
+      G[0] = 1.0;
+      co->hc[0] = h00;
+      co->cp[0] = 0.0;
+      co->sprev = s0;
+      co->hjj = h00;
+      st->m_done = 0;
+      if (!isfinite(h00) || !isfinite(an)) {
+        st->status = KX_ENONFINITE;
+        st->done = 1;
+      } else if (an > st->wmax) {
+        st->wmax = an;
+      }
+    }
+    return;
+  }
+  if (tid == 0) {
+    const double b = sqrt(__ldcg(&co->tot[2 * j]));
+    int stop = 0;
+    double sig = 0.0;
+    if (!isfinite(b)) stop = 2;
+    else if (b <= btol * st->wmax) stop = 1;   // invariant subspace: the projection is exact
+    else sig = 1.0 / b;
+    s.H[j + (int64_t)(j - 1) * ldh] = b;
+    s.scale[j] = sig;
+    st->m_done = j;
+    if (stop == 2) st->status = KX_ENONFINITE;
+    if (stop) st->done = 1;
+    sh_beta = b;
+    sh_sig = sig;
+    sh_stop = stop || final_step;
+  }
+  __syncthreads();
+  if (sh_stop) return;
+  const double beta = sh_beta, sig = sh_sig;
+  for (int i = tid; i < j; i += blockDim.x) {
+    const double si = s.scale[i];
+    const double gi = (si * __ldcg(&co->tot[j + i]) - __ldcg(&co->uh[i])) / beta;
+    const double hi = (si * __ldcg(&co->tot[i]) - __ldcg(&co->uc[i])) / beta;
+    G[i + (int64_t)j * LG] = gi;
+    G[j + (int64_t)i * LG] = gi;
+    sh_h[i] = hi;
+  }
+  if (tid == 0) {
+    const double hjj = sig * sig * __ldcg(&co->tot[2 * j + 1]);
+    const double an = sig * sqrt(__ldcg(&co->tot[2 * j + 2]));
+    sh_h[j] = hjj;
+    G[j + (int64_t)j * LG] = 1.0;
+    if (!isfinite(an)) {
+      st->status = KX_ENONFINITE;
+      st->done = 1;
+    } else if (an > st->wmax) {
+      st->wmax = an;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i <= j; i += blockDim.x) {
+    const double h = sh_h[i];
+    if (!isfinite(h)) {
+      st->status = KX_ENONFINITE;
+      st->done = 1;
+    }
+    s.H[i + (int64_t)j * ldh] = h;
+    co->hc[i] = h;
+  }
+  // c'_k = sum_{i<j} H(k, i) h_{i,j}, k <= j (H(k, i) = 0 for k > i + 1), four
+  // threads a row; H(j, j-1) = beta was written by thread 0 before the barrier
+  const int rstep = blockDim.x >> 2;
+  for (int r0 = 0; r0 <= j; r0 += rstep) {
+    const int row = r0 + (tid >> 2), part = tid & 3;
+    double cv = 0.0;
+    if (row <= j) {
+#pragma unroll 4
+      for (int i = max(row - 1, 0) + part; i < j; i += 4) cv += s.H[row + (int64_t)i * ldh] * sh_h[i];
+    }
+    cv = quad_sum(cv);
+    if (row <= j && part == 0) co->cp[row] = cv;
+  }
+  if (tid == 0) {
+    co->sprev = sig;
+    co->hjj = sh_h[j];
+  }
+}
+
+// Sum over b < nb of part[col * ps + b] in a fixed order, to every thread.
+__device__ __forceinline__ double block_column_sum(const double* part, int ps, int col, int nb) {
+  __shared__ double red[NWARPS];
+  __shared__ double res;
+  double x = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) x += __ldcg(part + (int64_t)col * ps + b);
+  x = warp_sum(x);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < NWARPS; ++w) t += red[w];
+    res = t;
+  }
+  __syncthreads();
+  return res;
+}
+
+// The work of apply pass K_j after its stencil: j == 0 the block partials
+// of its dots (d0 = V_0 . t, d1 = t . t); j >= 1 sweep S_j's partial columns
+// reduced (one column a block) and the Gram-row products uh, uc of rows
+// i < j (one warp a row).  The last block to finish finalises step j.
+template <typename T>
+__device__ __forceinline__ void sw_apply_tail(const Slot<T>& s, const SwSlot& w, int j, int ldh, int nbs,
+                                              double btol, double d0, double d1) {
+  if (j == 0) {
+    block_partial(d0, w.part, w.ps, 0);
+    block_partial(d1, w.part, w.ps, 1);
+  } else {
+    for (int col = blockIdx.x; col < 2 * j + 3; col += gridDim.x) {
+      const double x = block_column_sum(w.part, w.ps, col, nbs);
+      if (threadIdx.x == 0) w.co->tot[col] = x;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int row = blockIdx.x * NWARPS + warp; row < j; row += gridDim.x * NWARPS) {
+      double uh = 0.0, uc = 0.0;
+      for (int l = row + lane; l < j; l += 32) {
+        const double gil = w.G[row + (int64_t)l * LG];
+        uh += gil * w.co->hc[l];
+        uc += gil * w.co->cp[l];
+      }
+      uh = warp_sum(uh);
+      uc = warp_sum(uc);
+      if (lane == 0) {
+        w.co->uh[row] = uh;
+        w.co->uc[row] = uc;
+      }
+    }
+  }
+  if (!last_block(&w.co->counter)) return;
+  if (j == 0) {
+    for (int col = 0; col < 2; ++col) {
+      const double x = block_column_sum(w.part, w.ps, col, gridDim.x);
+      if (threadIdx.x == 0) w.co->tot[col] = x;
+    }
+    __syncthreads();
+  }
+  sw_fin<T>(s, w.co, w.G, j, ldh, btol, 0);
+  if (threadIdx.x == 0) w.co->counter = 0u;
+}
+
+// Apply pass K_j, any model and precision, one cell a thread: t = A V_j.
+template <typename T, int DIM, typename Mat>
+__global__ void __launch_bounds__(NTHREADS) k_sw_apply(Geo g, Slot<T> s, SwSlot w, int j, int64_t ld, Mat mat,
+                                                      int ldh, int nbs, double btol) {
+  pdl_enter();
+  if (s.st->done || s.st->retired) return;
+  constexpr int NC = ncomp_of(DIM);
+  const T* __restrict__ v = s.V + (int64_t)j * ld;
+  T* __restrict__ t = (T*)w.t;
+  const int64_t nc = g.ncell;
+  double d0 = 0.0, d1 = 0.0;
+  for (int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cell < nc;
+       cell += (int64_t)gridDim.x * blockDim.x) {
+    const Cell q = make_cell(g, cell);
+    T o[NC];
+    stencil<T, DIM, 0>(g, v, mat, q, o);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) t[(int64_t)c * nc + cell] = o[c];
+    if (j == 0) {
+      T a = T(0), b = T(0);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        a += v[(int64_t)c * nc + cell] * o[c];
+        b += o[c] * o[c];
+      }
+      d0 += (double)a;
+      d1 += (double)b;
+    }
+  }
+  sw_apply_tail<T>(s, w, j, ldh, nbs, btol, d0, d1);
+}
+
+// Apply pass K_j, 3D FP32, one quad of x-cells a thread (nx % 4 == 0).
+__global__ void __launch_bounds__(NTHREADS) k_sw_apply4(Geo g, Slot<float> s, SwSlot w, int j, int64_t ld,
+                                                       const float* __restrict__ ie, const float* __restrict__ sig2,
+                                                       int ldh, int nbs, double btol) {
+  pdl_enter();
+  if (s.st->done || s.st->retired) return;
+  const float* __restrict__ v = s.V + (int64_t)j * ld;
+  float* __restrict__ t = (float*)w.t;
+  const int64_t nc = g.ncell, nq = nc >> 2;
+  double d0 = 0.0, d1 = 0.0;
+  for (int64_t q4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q4 < nq; q4 += (int64_t)gridDim.x * blockDim.x) {
+    const Quad qd = make_quad(g, q4);
+    float4 o[6];
+    stencil_quad(g, v, ie, sig2, qd, o);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) *reinterpret_cast<float4*>(t + c * nc + qd.c0) = o[c];
+    if (j == 0) {
+      float a = 0.f, b = 0.f;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        a += dot4(ld4(v + c * nc + qd.c0), o[c]);
+        b += dot4(o[c], o[c]);
+      }
+      d0 += (double)a;
+      d1 += (double)b;
+    }
+  }
+  sw_apply_tail<float>(s, w, j, ldh, nbs, btol, d0, d1);
+}
+
+// Loads and arithmetic of CH basis columns cb .. cb+CH-1 for one cell: for
+// each column the dots with the current y and x, then its removal from both.
+// FULL: all CH columns exist (no per-column test).  An inactive thread
+// (act false) removes nothing, so its x and y stay zero and so do its dots.
+template <typename T, int NC, int CH, bool FULL>
+__device__ __forceinline__ void sw_columns(const T* __restrict__ V, int64_t ld, int64_t nc, int64_t cell, int cb,
+                                           int j, const T* ch, const T* cc, bool act, T* x, T* y, T* pa, T* pb) {
+  T vv[CH][NC];
+#pragma unroll
+  for (int k = 0; k < CH; ++k) {
+    if (FULL || cb + k < j) {
+      const T* __restrict__ vc = V + (int64_t)(cb + k) * ld + cell;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) vv[k][c] = vc[(int64_t)c * nc];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CH; ++k) {
+    pa[k] = T(0);
+    pb[k] = T(0);
+    if (FULL || cb + k < j) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        pa[k] += vv[k][c] * y[c];
+        pb[k] += vv[k][c] * x[c];
+      }
+      const T a = act ? ch[cb + k] : T(0), b = act ? cc[cb + k] : T(0);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        x[c] -= a * vv[k][c];
+        y[c] -= b * vv[k][c];
+      }
+    }
+  }
+}
+
+// Sweep S_j (j >= 1), any model and precision, one cell a thread.  Writes
+// V_j = x and the block partials of [a'_0..a'_{j-1}, b'_0..b'_{j-1}, x.x, x.y, y.y].
+template <typename T, int DIM, typename Mat>
+__global__ void __launch_bounds__(NTHREADS) k_sw_pass(Geo g, Slot<T> s, SwSlot w, int j, int64_t ld, Mat mat) {
+  pdl_enter();
+  if (s.st->done || s.st->retired) return;
+  constexpr int NC = ncomp_of(DIM);
+  constexpr int CH = sizeof(T) == 4 ? 8 : 4;   // basis columns in flight per thread
+  __shared__ T ch[MMAX], cc[MMAX];
+  __shared__ double acc[NWARPS][SWCOLS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = threadIdx.x; q < NWARPS * SWCOLS; q += blockDim.x) (&acc[0][0])[q] = 0.0;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    const double sc = s.scale[i];
+    ch[i] = (T)(w.co->hc[i] * sc);
+    cc[i] = (T)(w.co->cp[i] * sc);
+  }
+  const T sp = (T)w.co->sprev, hjj = (T)w.co->hjj;
+  __syncthreads();
+  const T* __restrict__ t = (const T*)w.t;
+  T* __restrict__ xout = s.V + (int64_t)j * ld;
+  const int64_t nc = g.ncell;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nc; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = base + threadIdx.x;
+    const bool act = cell < nc;
+    T x[NC], y[NC];
+    if (act) {
+      const Cell q = make_cell(g, cell);
+      T at[NC];
+      stencil<T, DIM, 0>(g, t, mat, q, at);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        x[c] = sp * t[(int64_t)c * nc + cell];
+        y[c] = sp * at[c] - hjj * x[c];
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) x[c] = y[c] = T(0);
+    }
+    // an inactive thread reads cell 0 (in bounds), removes nothing and
+    // contributes zero dots
+    const int64_t cl = act ? cell : 0;
+    for (int cb = 0; cb < j; cb += CH) {
+      T pa[CH], pb[CH];
+      if (cb + CH <= j) sw_columns<T, NC, CH, true>(s.V, ld, nc, cl, cb, j, ch, cc, act, x, y, pa, pb);
+      else sw_columns<T, NC, CH, false>(s.V, ld, nc, cl, cb, j, ch, cc, act, x, y, pa, pb);
+#pragma unroll
+      for (int k = 0; k < CH; ++k) {
+        pa[k] = warp_sum(pa[k]);
+        pb[k] = warp_sum(pb[k]);
+      }
+      if (lane < CH && cb + lane < j) {
+        T ma = pa[0], mb = pb[0];
+#pragma unroll
+        for (int k = 1; k < CH; ++k)
+          if (lane == k) {
+            ma = pa[k];
+            mb = pb[k];
+          }
+        acc[warp][cb + lane] += (double)ma;
+        acc[warp][j + cb + lane] += (double)mb;
+      }
+    }
+    T xx = T(0), xy = T(0), yy = T(0);
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        xout[(int64_t)c * nc + cell] = x[c];
+        xx += x[c] * x[c];
+        xy += x[c] * y[c];
+        yy += y[c] * y[c];
+      }
+    }
+    xx = warp_sum(xx);
+    xy = warp_sum(xy);
+    yy = warp_sum(yy);
+    if (lane == 0) {
+      acc[warp][2 * j] += (double)xx;
+      acc[warp][2 * j + 1] += (double)xy;
+      acc[warp][2 * j + 2] += (double)yy;
+    }
+  }
+  __syncthreads();
+  for (int col = threadIdx.x; col < 2 * j + 3; col += blockDim.x) {
+    double tsum = 0.0;
+#pragma unroll
+    for (int q = 0; q < NWARPS; ++q) tsum += acc[q][col];
+    w.part[(int64_t)col * w.ps + blockIdx.x] = tsum;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sweep S_j, 3D FP32, one quad of x-cells a thread (nx % 4 == 0): 16-byte
+// loads, SW_CH4 basis columns in flight (6 loads a column), packed two-lane
+// FMAs, and one transposed warp reduction for the dots of a chunk.
+constexpr int SW_CH4 = 1;     // basis columns a thread loads at once
+constexpr int SW_MINB4 = 2;   // resident blocks per SM the register budget allows
+static_assert(SW_CH4 == 1 || SW_CH4 == 2, "one or two columns at once");
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 join2(const float2& a, const float2& b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+// Warp sums of four values in a fixed order: lane l ends with the sum of
+// value (l >> 3) & 3, so lanes 0, 8, 16, 24 hold the sums of v0 .. v3.
+__device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v3, int lane) {
+  const bool b4 = (lane & 16) != 0;
+  const float r0 = (b4 ? v2 : v0) + __shfl_xor_sync(0xffffffffu, b4 ? v0 : v2, 16);
+  const float r1 = (b4 ? v3 : v1) + __shfl_xor_sync(0xffffffffu, b4 ? v1 : v3, 16);
+  const bool b3 = (lane & 8) != 0;
+  float r = (b3 ? r1 : r0) + __shfl_xor_sync(0xffffffffu, b3 ? r0 : r1, 8);
+  r += __shfl_xor_sync(0xffffffffu, r, 4);
+  r += __shfl_xor_sync(0xffffffffu, r, 2);
+  r += __shfl_xor_sync(0xffffffffu, r, 1);
+  return r;
+}
+
+// Warp sums of two values: lane l ends with the sum of value (l >> 4) & 1.
+__device__ __forceinline__ float warp_sum2(float v0, float v1, int lane) {
+  const bool b4 = (lane & 16) != 0;
+  float r = (b4 ? v1 : v0) + __shfl_xor_sync(0xffffffffu, b4 ? v0 : v1, 16);
+  r += __shfl_xor_sync(0xffffffffu, r, 8);
+  r += __shfl_xor_sync(0xffffffffu, r, 4);
+  r += __shfl_xor_sync(0xffffffffu, r, 2);
+  r += __shfl_xor_sync(0xffffffffu, r, 1);
+  return r;
+}
+
+template <int CH, bool FULL>
+__device__ __forceinline__ void sw_columns4(const float* __restrict__ V, int64_t ld, int64_t nc, int64_t c0, int cb,
+                                            int j, const float* ch, const float* cc, bool act, float4* x, float4* y,
+                                            float* pa, float* pb) {
+  float4 vv[CH][6];
+#pragma unroll
+  for (int k = 0; k < CH; ++k) {
+    if (FULL || cb + k < j) {
+      const float* __restrict__ vc = V + (int64_t)(cb + k) * ld + c0;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) vv[k][c] = ld4(vc + c * nc);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CH; ++k) {
+    pa[k] = 0.f;
+    pb[k] = 0.f;
+    if (FULL || cb + k < j) {
+      float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        sa = __ffma2_rn(lo2(vv[k][c]), lo2(y[c]), sa);
+        sa = __ffma2_rn(hi2(vv[k][c]), hi2(y[c]), sa);
+        sb = __ffma2_rn(lo2(vv[k][c]), lo2(x[c]), sb);
+        sb = __ffma2_rn(hi2(vv[k][c]), hi2(x[c]), sb);
+      }
+      pa[k] = sa.x + sa.y;
+      pb[k] = sb.x + sb.y;
+      const float a = act ? -ch[cb + k] : 0.f, b = act ? -cc[cb + k] : 0.f;
+      const float2 na = make_float2(a, a), nb = make_float2(b, b);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        x[c] = join2(__ffma2_rn(na, lo2(vv[k][c]), lo2(x[c])), __ffma2_rn(na, hi2(vv[k][c]), hi2(x[c])));
+        y[c] = join2(__ffma2_rn(nb, lo2(vv[k][c]), lo2(y[c])), __ffma2_rn(nb, hi2(vv[k][c]), hi2(y[c])));
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NTHREADS, SW_MINB4) k_sw_pass4(Geo g, Slot<float> s, SwSlot w, int j, int64_t ld,
+                                                         const float* __restrict__ ie,
+                                                         const float* __restrict__ sig2) {
+  pdl_enter();
+  if (s.st->done || s.st->retired) return;
+  __shared__ float ch[MMAX], cc[MMAX];
+  __shared__ double acc[NWARPS][SWCOLS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = threadIdx.x; q < NWARPS * SWCOLS; q += blockDim.x) (&acc[0][0])[q] = 0.0;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    const double sc = s.scale[i];
+    ch[i] = (float)(w.co->hc[i] * sc);
+    cc[i] = (float)(w.co->cp[i] * sc);
+  }
+  const float sp = (float)w.co->sprev, hjj = (float)w.co->hjj;
+  __syncthreads();
+  const float* __restrict__ t = (const float*)w.t;
+  float* __restrict__ xout = s.V + (int64_t)j * ld;
+  const int64_t nc = g.ncell, nq = nc >> 2;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nq; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q4 = base + threadIdx.x;
+    const bool act = q4 < nq;
+    float4 x[6], y[6];
+    // an inactive thread reads quad 0 (in bounds), removes nothing and
+    // contributes zero dots
+    int64_t c0 = 0;
+    if (act) {
+      const Quad qd = make_quad(g, q4);
+      c0 = qd.c0;
+      float4 at[6];
+      stencil_quad(g, t, ie, sig2, qd, at);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const float4 tv = ld4(t + c * nc + c0);
+        x[c] = make_float4(sp * tv.x, sp * tv.y, sp * tv.z, sp * tv.w);
+        y[c] = make_float4(sp * at[c].x - hjj * x[c].x, sp * at[c].y - hjj * x[c].y, sp * at[c].z - hjj * x[c].z,
+                           sp * at[c].w - hjj * x[c].w);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) x[c] = y[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int cb = 0; cb < j; cb += SW_CH4) {
+      float pa[SW_CH4], pb[SW_CH4];
+      if (cb + SW_CH4 <= j) sw_columns4<SW_CH4, true>(s.V, ld, nc, c0, cb, j, ch, cc, act, x, y, pa, pb);
+      else sw_columns4<SW_CH4, false>(s.V, ld, nc, c0, cb, j, ch, cc, act, x, y, pa, pb);
+      if constexpr (SW_CH4 == 2) {
+        const float r = warp_sum4(pa[0], pa[1], pb[0], pb[1], lane);
+        if ((lane & 7) == 0) {
+          const int q = lane >> 3;               // 0, 1: a' of columns cb, cb+1;  2, 3: b'
+          const int col = cb + (q & 1);
+          if (col < j) acc[warp][(q >> 1) * j + col] += (double)r;
+        }
+      } else {
+        const float r = warp_sum2(pa[0], pb[0], lane);
+        if ((lane & 15) == 0) acc[warp][(lane >> 4) * j + cb] += (double)r;
+      }
+    }
+    float xx = 0.f, xy = 0.f, yy = 0.f;
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        *reinterpret_cast<float4*>(xout + c * nc + c0) = x[c];
+        xx += dot4(x[c], x[c]);
+        xy += dot4(x[c], y[c]);
+        yy += dot4(y[c], y[c]);
+      }
+    }
+    xx = warp_sum(xx);
+    xy = warp_sum(xy);
+    yy = warp_sum(yy);
+    if (lane == 0) {
+      acc[warp][2 * j] += (double)xx;
+      acc[warp][2 * j + 1] += (double)xy;
+      acc[warp][2 * j + 2] += (double)yy;
+    }
+  }
+  __syncthreads();
+  for (int col = threadIdx.x; col < 2 * j + 3; col += blockDim.x) {
+    double tsum = 0.0;
+#pragma unroll
+    for (int q = 0; q < NWARPS; ++q) tsum += acc[q][col];
+    w.part[(int64_t)col * w.ps + blockIdx.x] = tsum;
+  }
+}
+
+// Finalisation after the last sweep S_m (one block): beta_{m-1}, scale_m,
+// m_done = m and the breakdown test.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_sw_last(Slot<T> s, SwSlot w, int m, int ldh, int nbs, double btol) {
+  pdl_enter();
+  if (s.st->done || s.st->retired) return;
+  const double x = block_column_sum(w.part, w.ps, 2 * m, nbs);
+  if (threadIdx.x == 0) w.co->tot[2 * m] = x;
+  __syncthreads();
+  sw_fin<T>(s, w.co, w.G, m, ldh, btol, 1);
+}
+
+}  // namespace
+
+template <typename T>
+constexpr double sw_btol() { return sizeof(T) == 8 ? 1e-12 : 1e-6; }
+
+static SwSlot sw_slot(kx_ctx* c, int slot) {
+  SwSlot w;
+  w.part = c->d_swpart + (int64_t)slot * SWCOLS * c->ps;
+  w.ps = c->ps;
+  w.G = c->d_swG + (int64_t)slot * LG * LG;
+  w.co = c->d_swco + slot;
+  w.t = c->d_swT;
+  return w;
+}
+
+// Persistent grids (occupancy x SMs, capped by the work and the partial
+// stride), shrunk for resident CTAs of kernels running beside the process.
+static void sw_grids(kx_ctx* c, const void* fa, const void* fs, int kind, int64_t items, int* nb_apply,
+                     int* nb_sweep) {
+  static std::atomic<int> ga[8], gs[8];
+  if (!ga[kind]) ga[kind] = persistent_grid(c, fa, 1 << 30, 0);
+  if (!gs[kind]) gs[kind] = persistent_grid(c, fs, 1 << 30, 0);
+  const int64_t rounds = (items + NTHREADS - 1) / NTHREADS;
+  *nb_apply = reserve_grid(c, (int)std::min<int64_t>(rounds, ga[kind].load()), ga[kind].load());
+  *nb_sweep = reserve_grid(c, (int)std::min<int64_t>(rounds, gs[kind].load()), gs[kind].load());
+}
+
+template <typename T, int DIM>
+static kx_status sweep_t(kx_ctx* c, int slot, int m) {
+  const Geo& g = c->geo;
+  const Slot<T> s = make_slot<T>(c, slot);
+  const SwSlot w = sw_slot(c, slot);
+  const T* ie = (const T*)c->d_inv_eps;
+  const T* sg = (const T*)c->d_sig2;
+  const TableMat<T> mat{ie, sg};
+  const int ldh = c->m + 1;
+  const double bt = sw_btol<T>();
+  // the quad kernels need 16-byte aligned rows of every array they read
+  constexpr bool f3 = sizeof(T) == 4 && DIM == 3;
+  const bool quad = f3 && (g.nx % 4) == 0;
+  int nba = 0, nbs = 0;
+  if (quad)
+    sw_grids(c, (const void*)k_sw_apply4, (const void*)k_sw_pass4, 7, g.ncell / 4, &nba, &nbs);
+  else
+    sw_grids(c, (const void*)k_sw_apply<T, DIM, TableMat<T>>, (const void*)k_sw_pass<T, DIM, TableMat<T>>,
+             (sizeof(T) == 8 ? 3 : 0) + (DIM - 2), g.ncell, &nba, &nbs);
+  const double vb = (double)c->n * c->esize;
+  const double mb = (double)g.ne * g.ncell * c->esize;
+  for (int j = 0; j <= m; ++j) {
+    if (j >= 1) {
+      time_begin(c);
+      if constexpr (f3) {
+        if (quad)
+          launch_k(c, k_sw_pass4, dim3(nbs), dim3(NTHREADS), 0, c->stream, g, (Slot<float>)s, w, j, c->ld,
+                   (const float*)ie, (const float*)sg);
+        else
+          launch_k(c, k_sw_pass<T, DIM, TableMat<T>>, dim3(nbs), dim3(NTHREADS), 0, c->stream, g, s, w, j, c->ld,
+                   mat);
+      } else {
+        launch_k(c, k_sw_pass<T, DIM, TableMat<T>>, dim3(nbs), dim3(NTHREADS), 0, c->stream, g, s, w, j, c->ld, mat);
+      }
+      time_end(c, KX_K_SWEEP, (j + 2.0) * vb + mb);
+      KX_CHECK_LAUNCH(c);
+    }
+    time_begin(c);
+    if (j == m) {
+      launch_k(c, k_sw_last<T>, dim3(1), dim3(NTHREADS), 0, c->stream, s, w, m, ldh, nbs, bt);
+    } else if constexpr (f3) {
+      if (quad)
+        launch_k(c, k_sw_apply4, dim3(nba), dim3(NTHREADS), 0, c->stream, g, (Slot<float>)s, w, j, c->ld,
+                 (const float*)ie, (const float*)sg, ldh, nbs, bt);
+      else
+        launch_k(c, k_sw_apply<T, DIM, TableMat<T>>, dim3(nba), dim3(NTHREADS), 0, c->stream, g, s, w, j, c->ld, mat,
+                 ldh, nbs, bt);
+    } else {
+      launch_k(c, k_sw_apply<T, DIM, TableMat<T>>, dim3(nba), dim3(NTHREADS), 0, c->stream, g, s, w, j, c->ld, mat,
+               ldh, nbs, bt);
+    }
+    time_end(c, KX_K_SWAPPLY, j < m ? 2.0 * vb + mb : 0.0);
+    KX_CHECK_LAUNCH(c);
+  }
+  c->stats.arnoldi_steps += m;
+  c->stats.matvecs += 2 * (int64_t)m;
+  return KX_OK;
+}
+
+kx_status sweep_arnoldi(kx_ctx* c, int slot, int m) {
+  const Geo& g = c->geo;
+  const bool fp64 = c->d.precision == KX_FP64;
+  if (g.dim == 3) return fp64 ? sweep_t<double, 3>(c, slot, m) : sweep_t<float, 3>(c, slot, m);
+  if (g.pml) return fp64 ? sweep_t<double, 4>(c, slot, m) : sweep_t<float, 4>(c, slot, m);
+  return fp64 ? sweep_t<double, 2>(c, slot, m) : sweep_t<float, 2>(c, slot, m);
+}
+
+}  // namespace kx
