@@ -369,6 +369,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--arnoldi", default="default", choices=["default", "twopass", "sweep"],
+                    help="Arnoldi form of the timed contexts (descriptor arnoldi_form)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -387,7 +389,7 @@ def main():
     stream = torch.cuda.Stream()
     ctx = Context(sc.grid, sc.eps_cell, precision=w["prec"], krylov_dim=w["m"],
                   max_freqs=w["nfreq"], batch=w.get("batch", 1), stream=stream,
-                  rst_samples=w.get("rst_samples", 0))
+                  rst_samples=w.get("rst_samples", 0), arnoldi=args.arnoldi)
     g_host = torch.tensor(sc.g, dtype=dt).pin_memory()
     g = g_host.to("cuda")
     torch.cuda.synchronize()
@@ -504,7 +506,7 @@ def main():
     single = None
     if w.get("batch", 1) > 1 or w["method"] == "rstdim":
         ctx1 = Context(sc.grid, sc.eps_cell, precision=w["prec"], krylov_dim=w["m"], max_freqs=1,
-                       batch=1, stream=stream, rst_samples=w.get("rst_samples", 0))
+                       batch=1, stream=stream, rst_samples=w.get("rst_samples", 0), arnoldi=args.arnoldi)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
@@ -528,7 +530,7 @@ def main():
                 "dtype": "f32" if w["prec"] == "fp32" else "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "grid": list(sc.grid.n), "unknowns": sc.grid.nunk,
                            "T": w["T"], "krylov_dim": w["m"], "nfreq": w["nfreq"], "method": w["method"],
-                           "projected": "f64", "parallelism": f"replicas{world}",
+                           "projected": "f64", "arnoldi": args.arnoldi, "parallelism": f"replicas{world}",
                            "l2": "working set (Krylov basis) larger than L2; no flush"},
                 "roofline": roofline,
                 "arnoldi_hbm_gbs": round(ab_gbs, 1),

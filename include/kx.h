@@ -54,8 +54,10 @@ enum { KX_FP64 = 0, KX_FP32 = 1 };
 enum { KX_PLAIN = 0, KX_SPLIT = 1, KX_RSTDIM = 2, KX_SPLIT2 = 3, KX_SPLIT4D = 4 };
 /* Form of the Arnoldi process (kx_desc.arnoldi_form).  Both are classical
  * Gram-Schmidt (Sect. 3.2, eq. (Arn)) and agree up to rounding.
- *   KX_ARN_DEFAULT: the single-sweep form for restart in Krylov dimension,
- *                   the two-pass form everywhere else.
+ *   KX_ARN_DEFAULT: the single-sweep form for restart in Krylov dimension
+ *                   on grids of 3e6 unknowns or more (where it is the
+ *                   faster of the two on GB300), the two-pass form
+ *                   everywhere else.
  *   KX_ARN_TWOPASS: per step, one pass applies A fused with the dots
  *                   V_j^T A v_j, a second applies the update and the norm;
  *                   the basis is read twice.

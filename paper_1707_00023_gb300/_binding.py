@@ -128,8 +128,9 @@ class Context:
     problems, since torch hands out streams from a small pool).
     ``rst_samples``: time samples per frequency held for the restart-in-
     dimension method (``method="rstdim"``; 0 leaves it unavailable).
-    ``arnoldi``: "default" (single sweep for restart in dimension, two passes
-    elsewhere), "twopass" or "sweep" (also for ``arnoldi()``).
+    ``arnoldi``: "default" (single sweep for restart in dimension on grids of
+    3e6 unknowns or more, two passes elsewhere), "twopass" or "sweep" (also
+    for ``arnoldi()``).
     """
 
     def __init__(self, grid, eps_cell, precision: str = "fp32", krylov_dim: int = 64,

@@ -892,11 +892,21 @@ kx_status response_at_freqs(kx_ctx* c, const void* d_g, const double* omegas, in
 }
 
 // The Arnoldi process of one restart in Krylov dimension (basis slot
-// `slot`, non-augmented): the single-sweep form unless the descriptor asks
-// for the two-pass form.
+// `slot`, non-augmented).  By default the single-sweep form runs from
+// SWEEP_MIN_UNKNOWNS unknowns up: its serial per-step finalisation (a few
+// microseconds) hides behind the apply pass only on large grids (measured on
+// GB300: at 64^3 the two-pass form is faster, from 96^3 up the single sweep).
+constexpr int64_t SWEEP_MIN_UNKNOWNS = 3000000;
+
+bool rst_uses_sweep(const kx_ctx* c) {
+  if (c->d.arnoldi_form == KX_ARN_SWEEP) return true;
+  if (c->d.arnoldi_form == KX_ARN_TWOPASS) return false;
+  return c->n >= SWEEP_MIN_UNKNOWNS;
+}
+
 kx_status rst_arnoldi(kx_ctx* c, int slot) {
-  if (c->d.arnoldi_form == KX_ARN_TWOPASS) return arnoldi_steps(c, slot, 1, c->m, nullptr);
-  return sweep_arnoldi(c, slot, c->m);
+  if (rst_uses_sweep(c)) return sweep_arnoldi(c, slot, c->m);
+  return arnoldi_steps(c, slot, 1, c->m, nullptr);
 }
 
 kx_status response_restart_dim(kx_ctx* c, const void* d_g, const double* omegas, int nfreq, double T,
@@ -1031,6 +1041,8 @@ kx_status response_restart_dim(kx_ctx* c, const void* d_g, const double* omegas,
     KX_CUDA(c, cudaStreamSynchronize(Bs), "stream synchronise");
     if (*h_status) {
       sync(c);
+      if (*h_status == KX_ETIMEOUT)
+        return fail(c, KX_ETIMEOUT, "Arnoldi process: a bounded wait for a basis copy ran out");
       return fail(c, KX_ENONFINITE, "restart set-up: non-finite Arnoldi process or projected exponential");
     }
     all_stopped = true;

@@ -310,6 +310,13 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;" :::);
 }
 
+// The two halves of pdl_enter, for kernels that let their successor launch
+// only near their end: successor blocks launched early wait on the SMs and
+// would hold the room that kernels of another stream, running beside the
+// chain, need.  A block that exits counts as having triggered.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 template <typename... KArgs, typename... Args>
 inline void launch_k(const kx_ctx* c, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
                      cudaStream_t st, Args... args) {

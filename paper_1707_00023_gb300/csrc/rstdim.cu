@@ -88,7 +88,9 @@ __global__ void __launch_bounds__(256) k_rst_setup(const double* __restrict__ H,
   __shared__ int piv;
   const int md = st->m_done;
   if (md < 1 || st->status) {
-    if (threadIdx.x == 0) *status = KX_ENONFINITE;
+    // the Arnoldi process's own status (a non-finite value, a bounded wait
+    // that ran out), else no step completed
+    if (threadIdx.x == 0) *status = st->status ? st->status : KX_ENONFINITE;
     return;
   }
   // the six (m+6)-square work matrices live in global memory (L1/L2

@@ -59,10 +59,13 @@ __device__ __forceinline__ double quad_sum(double x) {
 //           beta_{j-1}, scale_j, m_done = j, the breakdown test, then
 //           (unless final_step or the process stopped) G column j, H column
 //           j and the coefficients of sweep S_{j+1}.
-// tot, uh and uc were written by other blocks of the same launch: read past L1.
+// Its inputs are first staged in shared memory in one parallel load phase
+// (the step's latency is this block's chain of dependent loads); tot, uh and
+// uc were written by other blocks of the same launch: read past L1.
 template <typename T>
 __device__ void sw_fin(const Slot<T>& s, SwCoef* co, double* G, int j, int ldh, double btol, int final_step) {
-  __shared__ double sh_h[MMAX + 1];
+  __shared__ double sh_tot[SWCOLS], sh_u[2][MMAX], sh_sc[MMAX], sh_h[MMAX + 1];
+  __shared__ double sh_H[LG * MMAX];   // the upper Hessenberg part of H(0:j, 0:j-1)
   __shared__ double sh_beta, sh_sig;
   __shared__ int sh_stop;
   SlotState* st = s.st;
@@ -88,8 +91,23 @@ __device__ void sw_fin(const Slot<T>& s, SwCoef* co, double* G, int j, int ldh, 
     }
     return;
   }
+  const bool full = !final_step;
+  for (int q = tid; q < 2 * j + 3; q += blockDim.x) sh_tot[q] = __ldcg(&co->tot[q]);
+  if (full) {
+    for (int q = tid; q < j; q += blockDim.x) {
+      sh_u[0][q] = __ldcg(&co->uh[q]);
+      sh_u[1][q] = __ldcg(&co->uc[q]);
+      sh_sc[q] = s.scale[q];
+    }
+    // H(k, i), k <= j, i < j, nonzero for i >= k - 1 (H(j, j-1) is set below)
+    for (int q = tid; q < (j + 1) * j; q += blockDim.x) {
+      const int k = q % (j + 1), i = q / (j + 1);
+      sh_H[k + i * LG] = (i >= k - 1 && k < j) ? s.H[k + (int64_t)i * ldh] : 0.0;
+    }
+  }
+  __syncthreads();
   if (tid == 0) {
-    const double b = sqrt(__ldcg(&co->tot[2 * j]));
+    const double b = sqrt(sh_tot[2 * j]);
     int stop = 0;
     double sig = 0.0;
     if (!isfinite(b)) stop = 2;
@@ -100,6 +118,7 @@ __device__ void sw_fin(const Slot<T>& s, SwCoef* co, double* G, int j, int ldh, 
     st->m_done = j;
     if (stop == 2) st->status = KX_ENONFINITE;
     if (stop) st->done = 1;
+    sh_H[j + (j - 1) * LG] = b;
     sh_beta = b;
     sh_sig = sig;
     sh_stop = stop || final_step;
@@ -108,16 +127,15 @@ __device__ void sw_fin(const Slot<T>& s, SwCoef* co, double* G, int j, int ldh, 
   if (sh_stop) return;
   const double beta = sh_beta, sig = sh_sig;
   for (int i = tid; i < j; i += blockDim.x) {
-    const double si = s.scale[i];
-    const double gi = (si * __ldcg(&co->tot[j + i]) - __ldcg(&co->uh[i])) / beta;
-    const double hi = (si * __ldcg(&co->tot[i]) - __ldcg(&co->uc[i])) / beta;
+    const double gi = (sh_sc[i] * sh_tot[j + i] - sh_u[0][i]) / beta;
+    const double hi = (sh_sc[i] * sh_tot[i] - sh_u[1][i]) / beta;
     G[i + (int64_t)j * LG] = gi;
     G[j + (int64_t)i * LG] = gi;
     sh_h[i] = hi;
   }
   if (tid == 0) {
-    const double hjj = sig * sig * __ldcg(&co->tot[2 * j + 1]);
-    const double an = sig * sqrt(__ldcg(&co->tot[2 * j + 2]));
+    const double hjj = sig * sig * sh_tot[2 * j + 1];
+    const double an = sig * sqrt(sh_tot[2 * j + 2]);
     sh_h[j] = hjj;
     G[j + (int64_t)j * LG] = 1.0;
     if (!isfinite(an)) {
@@ -137,15 +155,13 @@ __device__ void sw_fin(const Slot<T>& s, SwCoef* co, double* G, int j, int ldh, 
     s.H[i + (int64_t)j * ldh] = h;
     co->hc[i] = h;
   }
-  // c'_k = sum_{i<j} H(k, i) h_{i,j}, k <= j (H(k, i) = 0 for k > i + 1), four
-  // threads a row; H(j, j-1) = beta was written by thread 0 before the barrier
+  // c'_k = sum_{i<j} H(k, i) h_{i,j}, k <= j, four threads a row
   const int rstep = blockDim.x >> 2;
   for (int r0 = 0; r0 <= j; r0 += rstep) {
     const int row = r0 + (tid >> 2), part = tid & 3;
     double cv = 0.0;
     if (row <= j) {
-#pragma unroll 4
-      for (int i = max(row - 1, 0) + part; i < j; i += 4) cv += s.H[row + (int64_t)i * ldh] * sh_h[i];
+      for (int i = max(row - 1, 0) + part; i < j; i += 4) cv += sh_H[row + i * LG] * sh_h[i];
     }
     cv = quad_sum(cv);
     if (row <= j && part == 0) co->cp[row] = cv;
@@ -175,56 +191,78 @@ __device__ __forceinline__ double block_column_sum(const double* part, int ps, i
   return res;
 }
 
-// The work of apply pass K_j after its stencil: j == 0 the block partials
-// of its dots (d0 = V_0 . t, d1 = t . t); j >= 1 sweep S_j's partial columns
-// reduced (one column a block) and the Gram-row products uh, uc of rows
-// i < j (one warp a row).  The last block to finish finalises step j.
+// True in every thread of the last of `count` blocks to call it; that block
+// then sees the global writes the others made before their call.
+__device__ __forceinline__ bool last_of(unsigned* counter, unsigned count) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = atomicAdd(counter, 1u) == count - 1;
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+// Step j >= 1, at the start of apply pass K_j: the first R = min(grid,
+// 2j+3) blocks reduce sweep S_j's partial columns (one column a block) and
+// form the Gram-row products uh, uc of rows i < j (one warp a row); the last
+// of them finalises step j.  This runs beside the other blocks' stencil
+// work, which reads none of it.
 template <typename T>
-__device__ __forceinline__ void sw_apply_tail(const Slot<T>& s, const SwSlot& w, int j, int ldh, int nbs,
-                                              double btol, double d0, double d1) {
-  if (j == 0) {
-    block_partial(d0, w.part, w.ps, 0);
-    block_partial(d1, w.part, w.ps, 1);
-  } else {
-    for (int col = blockIdx.x; col < 2 * j + 3; col += gridDim.x) {
-      const double x = block_column_sum(w.part, w.ps, col, nbs);
-      if (threadIdx.x == 0) w.co->tot[col] = x;
+__device__ __forceinline__ void sw_apply_head(const Slot<T>& s, const SwSlot& w, int j, int ldh, int nbs,
+                                              double btol) {
+  const int R = min((int)gridDim.x, 2 * j + 3);
+  if ((int)blockIdx.x >= R) return;
+  for (int col = blockIdx.x; col < 2 * j + 3; col += R) {
+    const double x = block_column_sum(w.part, w.ps, col, nbs);
+    if (threadIdx.x == 0) w.co->tot[col] = x;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int row = blockIdx.x * NWARPS + warp; row < j; row += R * NWARPS) {
+    double uh = 0.0, uc = 0.0;
+    for (int l = row + lane; l < j; l += 32) {
+      const double gil = w.G[row + (int64_t)l * LG];
+      uh += gil * w.co->hc[l];
+      uc += gil * w.co->cp[l];
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int row = blockIdx.x * NWARPS + warp; row < j; row += gridDim.x * NWARPS) {
-      double uh = 0.0, uc = 0.0;
-      for (int l = row + lane; l < j; l += 32) {
-        const double gil = w.G[row + (int64_t)l * LG];
-        uh += gil * w.co->hc[l];
-        uc += gil * w.co->cp[l];
-      }
-      uh = warp_sum(uh);
-      uc = warp_sum(uc);
-      if (lane == 0) {
-        w.co->uh[row] = uh;
-        w.co->uc[row] = uc;
-      }
+    uh = warp_sum(uh);
+    uc = warp_sum(uc);
+    if (lane == 0) {
+      w.co->uh[row] = uh;
+      w.co->uc[row] = uc;
     }
   }
-  if (!last_block(&w.co->counter)) return;
-  if (j == 0) {
-    for (int col = 0; col < 2; ++col) {
-      const double x = block_column_sum(w.part, w.ps, col, gridDim.x);
-      if (threadIdx.x == 0) w.co->tot[col] = x;
-    }
-    __syncthreads();
-  }
+  if (!last_of(&w.co->counter, (unsigned)R)) return;
   sw_fin<T>(s, w.co, w.G, j, ldh, btol, 0);
   if (threadIdx.x == 0) w.co->counter = 0u;
 }
 
-// Apply pass K_j, any model and precision, one cell a thread: t = A V_j.
+// Step 0, at the end of apply pass K_0: the block partials of its dots
+// (d0 = V_0 . t, d1 = t . t); the last block reduces them and finalises.
+template <typename T>
+__device__ __forceinline__ void sw_apply_tail0(const Slot<T>& s, const SwSlot& w, int ldh, double btol, double d0,
+                                               double d1) {
+  block_partial(d0, w.part, w.ps, 0);
+  block_partial(d1, w.part, w.ps, 1);
+  if (!last_of(&w.co->counter, gridDim.x)) return;
+  for (int col = 0; col < 2; ++col) {
+    const double x = block_column_sum(w.part, w.ps, col, gridDim.x);
+    if (threadIdx.x == 0) w.co->tot[col] = x;
+  }
+  __syncthreads();
+  sw_fin<T>(s, w.co, w.G, 0, ldh, btol, 0);
+  if (threadIdx.x == 0) w.co->counter = 0u;
+}
+
+// Apply pass K_j, any model and precision, one cell a thread: t = A V_j
+// (with step j's finalisation beside it, or step 0's after it).
 template <typename T, int DIM, typename Mat>
 __global__ void __launch_bounds__(NTHREADS) k_sw_apply(Geo g, Slot<T> s, SwSlot w, int j, int64_t ld, Mat mat,
                                                       int ldh, int nbs, double btol) {
-  pdl_enter();
+  pdl_wait();
   if (s.st->done || s.st->retired) return;
   constexpr int NC = ncomp_of(DIM);
+  if (j >= 1) sw_apply_head<T>(s, w, j, ldh, nbs, btol);
   const T* __restrict__ v = s.V + (int64_t)j * ld;
   T* __restrict__ t = (T*)w.t;
   const int64_t nc = g.ncell;
@@ -247,15 +285,17 @@ __global__ void __launch_bounds__(NTHREADS) k_sw_apply(Geo g, Slot<T> s, SwSlot 
       d1 += (double)b;
     }
   }
-  sw_apply_tail<T>(s, w, j, ldh, nbs, btol, d0, d1);
+  pdl_trigger();
+  if (j == 0) sw_apply_tail0<T>(s, w, ldh, btol, d0, d1);
 }
 
 // Apply pass K_j, 3D FP32, one quad of x-cells a thread (nx % 4 == 0).
 __global__ void __launch_bounds__(NTHREADS) k_sw_apply4(Geo g, Slot<float> s, SwSlot w, int j, int64_t ld,
                                                        const float* __restrict__ ie, const float* __restrict__ sig2,
                                                        int ldh, int nbs, double btol) {
-  pdl_enter();
+  pdl_wait();
   if (s.st->done || s.st->retired) return;
+  if (j >= 1) sw_apply_head<float>(s, w, j, ldh, nbs, btol);
   const float* __restrict__ v = s.V + (int64_t)j * ld;
   float* __restrict__ t = (float*)w.t;
   const int64_t nc = g.ncell, nq = nc >> 2;
@@ -277,7 +317,8 @@ __global__ void __launch_bounds__(NTHREADS) k_sw_apply4(Geo g, Slot<float> s, Sw
       d1 += (double)b;
     }
   }
-  sw_apply_tail<float>(s, w, j, ldh, nbs, btol, d0, d1);
+  pdl_trigger();
+  if (j == 0) sw_apply_tail0<float>(s, w, ldh, btol, d0, d1);
 }
 
 // Loads and arithmetic of CH basis columns cb .. cb+CH-1 for one cell: for
@@ -320,7 +361,7 @@ __device__ __forceinline__ void sw_columns(const T* __restrict__ V, int64_t ld, 
 // V_j = x and the block partials of [a'_0..a'_{j-1}, b'_0..b'_{j-1}, x.x, x.y, y.y].
 template <typename T, int DIM, typename Mat>
 __global__ void __launch_bounds__(NTHREADS) k_sw_pass(Geo g, Slot<T> s, SwSlot w, int j, int64_t ld, Mat mat) {
-  pdl_enter();
+  pdl_wait();
   if (s.st->done || s.st->retired) return;
   constexpr int NC = ncomp_of(DIM);
   constexpr int CH = sizeof(T) == 4 ? 8 : 4;   // basis columns in flight per thread
@@ -398,6 +439,7 @@ __global__ void __launch_bounds__(NTHREADS) k_sw_pass(Geo g, Slot<T> s, SwSlot w
       acc[warp][2 * j + 2] += (double)yy;
     }
   }
+  pdl_trigger();
   __syncthreads();
   for (int col = threadIdx.x; col < 2 * j + 3; col += blockDim.x) {
     double tsum = 0.0;
@@ -408,31 +450,14 @@ __global__ void __launch_bounds__(NTHREADS) k_sw_pass(Geo g, Slot<T> s, SwSlot w
 }
 
 // ---------------------------------------------------------------------------
-// Sweep S_j, 3D FP32, one quad of x-cells a thread (nx % 4 == 0): 16-byte
-// loads, SW_CH4 basis columns in flight (6 loads a column), packed two-lane
-// FMAs, and one transposed warp reduction for the dots of a chunk.
-constexpr int SW_CH4 = 1;     // basis columns a thread loads at once
-constexpr int SW_MINB4 = 2;   // resident blocks per SM the register budget allows
-static_assert(SW_CH4 == 1 || SW_CH4 == 2, "one or two columns at once");
+// Helpers of the quad sweep below: float4 halves for the packed two-lane
+// FMAs, and a transposed warp reduction of two values.
 __device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
 __device__ __forceinline__ float4 join2(const float2& a, const float2& b) { return make_float4(a.x, a.y, b.x, b.y); }
 
-// Warp sums of four values in a fixed order: lane l ends with the sum of
-// value (l >> 3) & 3, so lanes 0, 8, 16, 24 hold the sums of v0 .. v3.
-__device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v3, int lane) {
-  const bool b4 = (lane & 16) != 0;
-  const float r0 = (b4 ? v2 : v0) + __shfl_xor_sync(0xffffffffu, b4 ? v0 : v2, 16);
-  const float r1 = (b4 ? v3 : v1) + __shfl_xor_sync(0xffffffffu, b4 ? v1 : v3, 16);
-  const bool b3 = (lane & 8) != 0;
-  float r = (b3 ? r1 : r0) + __shfl_xor_sync(0xffffffffu, b3 ? r0 : r1, 8);
-  r += __shfl_xor_sync(0xffffffffu, r, 4);
-  r += __shfl_xor_sync(0xffffffffu, r, 2);
-  r += __shfl_xor_sync(0xffffffffu, r, 1);
-  return r;
-}
-
-// Warp sums of two values: lane l ends with the sum of value (l >> 4) & 1.
+// Warp sums of two values in a fixed order: lane l ends with the sum of
+// value (l >> 4) & 1, so lanes 0 and 16 hold the sums of v0 and v1.
 __device__ __forceinline__ float warp_sum2(float v0, float v1, int lane) {
   const bool b4 = (lane & 16) != 0;
   float r = (b4 ? v1 : v0) + __shfl_xor_sync(0xffffffffu, b4 ? v0 : v1, 16);
@@ -443,50 +468,81 @@ __device__ __forceinline__ float warp_sum2(float v0, float v1, int lane) {
   return r;
 }
 
-template <int CH, bool FULL>
-__device__ __forceinline__ void sw_columns4(const float* __restrict__ V, int64_t ld, int64_t nc, int64_t c0, int cb,
-                                            int j, const float* ch, const float* cc, bool act, float4* x, float4* y,
-                                            float* pa, float* pb) {
-  float4 vv[CH][6];
-#pragma unroll
-  for (int k = 0; k < CH; ++k) {
-    if (FULL || cb + k < j) {
-      const float* __restrict__ vc = V + (int64_t)(cb + k) * ld + c0;
-#pragma unroll
-      for (int c = 0; c < 6; ++c) vv[k][c] = ld4(vc + c * nc);
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < CH; ++k) {
-    pa[k] = 0.f;
-    pb[k] = 0.f;
-    if (FULL || cb + k < j) {
-      float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        sa = __ffma2_rn(lo2(vv[k][c]), lo2(y[c]), sa);
-        sa = __ffma2_rn(hi2(vv[k][c]), hi2(y[c]), sa);
-        sb = __ffma2_rn(lo2(vv[k][c]), lo2(x[c]), sb);
-        sb = __ffma2_rn(hi2(vv[k][c]), hi2(x[c]), sb);
-      }
-      pa[k] = sa.x + sa.y;
-      pb[k] = sb.x + sb.y;
-      const float a = act ? -ch[cb + k] : 0.f, b = act ? -cc[cb + k] : 0.f;
-      const float2 na = make_float2(a, a), nb = make_float2(b, b);
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        x[c] = join2(__ffma2_rn(na, lo2(vv[k][c]), lo2(x[c])), __ffma2_rn(na, hi2(vv[k][c]), hi2(x[c])));
-        y[c] = join2(__ffma2_rn(nb, lo2(vv[k][c]), lo2(y[c])), __ffma2_rn(nb, hi2(vv[k][c]), hi2(y[c])));
-      }
-    }
-  }
+// ---------------------------------------------------------------------------
+// Sweep S_j, 3D FP32, with the basis staged through shared memory: a block
+// owns tiles of SW_TILE cells (one quad a thread) and, for each tile,
+// streams the columns V_0..V_{j-1} through a ring of SW_STAGES buffers that
+// one thread fills with one-dimensional bulk copies (cp.async.bulk, their
+// completion counted on an mbarrier per buffer).  The bytes in flight per SM
+// then no longer depend on registers: a register-fed form, with the 128
+// registers two blocks per SM allow, kept one column per warp in flight
+// (measured at 128^3: 0.79 of the measured copy bandwidth, staged 0.84).
+// Every wait is bounded: when one runs out the block records KX_ETIMEOUT,
+// waits (bounded again) for its own copies and returns.
+constexpr int SW_TILE = 4 * NTHREADS;                             // cells a tile
+constexpr int SW_STAGES = 4;                                      // buffers in the ring
+constexpr size_t SW_STAGE_FLOATS = 6 * (size_t)SW_TILE;           // one column of a tile
+constexpr size_t SW_SMEM = SW_STAGES * SW_STAGE_FLOATS * sizeof(float);
+constexpr unsigned SW_WAIT_LIMIT = 1u << 22;                      // try_wait rounds of one wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the completion of phase `parity` of b.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
+  for (unsigned k = 0; k < SW_WAIT_LIMIT; ++k)
+    if (mbar_test(b, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(b))
+               : "memory");
 }
 
-__global__ void __launch_bounds__(NTHREADS, SW_MINB4) k_sw_pass4(Geo g, Slot<float> s, SwSlot w, int j, int64_t ld,
-                                                         const float* __restrict__ ie,
-                                                         const float* __restrict__ sig2) {
-  pdl_enter();
+// Element e of a block's stream: column e % j of its tile e / j, into
+// buffer e % SW_STAGES (16-byte aligned: tiles start at multiples of 1024
+// cells, columns at multiples of 64 scalars, components at multiples of
+// ncell with ncell % 4 == 0; each copy is a multiple of 16 bytes).
+__device__ __forceinline__ void sw_issue(const Slot<float>& s, int64_t ld, int64_t nc, int j, int64_t e, float* ring,
+                                         uint64_t* full) {
+  const int64_t tile = blockIdx.x + (e / j) * gridDim.x;
+  const int col = (int)(e % j);
+  const int64_t cell0 = tile * SW_TILE;
+  const int64_t cells = nc - cell0 < SW_TILE ? nc - cell0 : SW_TILE;
+  const unsigned bytes = (unsigned)(cells * (int64_t)sizeof(float));
+  const int b = (int)(e % SW_STAGES);
+  float* dst = ring + b * SW_STAGE_FLOATS;
+  const float* src = s.V + (int64_t)col * ld + cell0;
+  mbar_expect_tx(&full[b], 6u * bytes);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) bulk_load(dst + c * SW_TILE, src + c * nc, bytes, &full[b]);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s, SwSlot w, int j, int64_t ld,
+                                                          const float* __restrict__ ie,
+                                                          const float* __restrict__ sig2) {
+  pdl_wait();
   if (s.st->done || s.st->retired) return;
+  extern __shared__ __align__(128) unsigned char sw_dyn[];
+  float* ring = reinterpret_cast<float*>(sw_dyn);
+  __shared__ __align__(8) uint64_t full[SW_STAGES];
   __shared__ float ch[MMAX], cc[MMAX];
   __shared__ double acc[NWARPS][SWCOLS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -497,74 +553,121 @@ __global__ void __launch_bounds__(NTHREADS, SW_MINB4) k_sw_pass4(Geo g, Slot<flo
     cc[i] = (float)(w.co->cp[i] * sc);
   }
   const float sp = (float)w.co->sprev, hjj = (float)w.co->hjj;
-  __syncthreads();
-  const float* __restrict__ t = (const float*)w.t;
-  float* __restrict__ xout = s.V + (int64_t)j * ld;
   const int64_t nc = g.ncell, nq = nc >> 2;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nq; base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t q4 = base + threadIdx.x;
-    const bool act = q4 < nq;
-    float4 x[6], y[6];
-    // an inactive thread reads quad 0 (in bounds), removes nothing and
-    // contributes zero dots
-    int64_t c0 = 0;
-    if (act) {
-      const Quad qd = make_quad(g, q4);
-      c0 = qd.c0;
-      float4 at[6];
-      stencil_quad(g, t, ie, sig2, qd, at);
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const float4 tv = ld4(t + c * nc + c0);
-        x[c] = make_float4(sp * tv.x, sp * tv.y, sp * tv.z, sp * tv.w);
-        y[c] = make_float4(sp * at[c].x - hjj * x[c].x, sp * at[c].y - hjj * x[c].y, sp * at[c].z - hjj * x[c].z,
-                           sp * at[c].w - hjj * x[c].w);
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < 6; ++c) x[c] = y[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    for (int cb = 0; cb < j; cb += SW_CH4) {
-      float pa[SW_CH4], pb[SW_CH4];
-      if (cb + SW_CH4 <= j) sw_columns4<SW_CH4, true>(s.V, ld, nc, c0, cb, j, ch, cc, act, x, y, pa, pb);
-      else sw_columns4<SW_CH4, false>(s.V, ld, nc, c0, cb, j, ch, cc, act, x, y, pa, pb);
-      if constexpr (SW_CH4 == 2) {
-        const float r = warp_sum4(pa[0], pa[1], pb[0], pb[1], lane);
-        if ((lane & 7) == 0) {
-          const int q = lane >> 3;               // 0, 1: a' of columns cb, cb+1;  2, 3: b'
-          const int col = cb + (q & 1);
-          if (col < j) acc[warp][(q >> 1) * j + col] += (double)r;
-        }
-      } else {
-        const float r = warp_sum2(pa[0], pb[0], lane);
-        if ((lane & 15) == 0) acc[warp][(lane >> 4) * j + cb] += (double)r;
-      }
-    }
-    float xx = 0.f, xy = 0.f, yy = 0.f;
-    if (act) {
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        *reinterpret_cast<float4*>(xout + c * nc + c0) = x[c];
-        xx += dot4(x[c], x[c]);
-        xy += dot4(x[c], y[c]);
-        yy += dot4(y[c], y[c]);
-      }
-    }
-    xx = warp_sum(xx);
-    xy = warp_sum(xy);
-    yy = warp_sum(yy);
-    if (lane == 0) {
-      acc[warp][2 * j] += (double)xx;
-      acc[warp][2 * j + 1] += (double)xy;
-      acc[warp][2 * j + 2] += (double)yy;
-    }
+  const int64_t ntiles = (nc + SW_TILE - 1) / SW_TILE;
+  const int64_t mine = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t E = mine * j;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < SW_STAGES; ++b) mbar_init(&full[b], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  for (int col = threadIdx.x; col < 2 * j + 3; col += blockDim.x) {
+  if (threadIdx.x == 0)
+    for (int64_t e = 0; e < E && e < SW_STAGES; ++e) sw_issue(s, ld, nc, j, e, ring, full);
+  const float* __restrict__ t = (const float*)w.t;
+  float* __restrict__ xout = s.V + (int64_t)j * ld;
+  float4 x[6], y[6];
+  bool act = false, ok = true;
+  int64_t c0 = 0, tile = blockIdx.x;
+  int col = 0;
+  for (int64_t e = 0; e < E; ++e) {
+    if (col == 0) {
+      // a tile starts: x = A v_{j-1}, y = A^2 v_{j-1} - h_{j-1,j-1} A v_{j-1}
+      const int64_t q4 = tile * NTHREADS + threadIdx.x;
+      act = q4 < nq;
+      c0 = 0;
+      if (act) {
+        const Quad qd = make_quad(g, q4);
+        c0 = qd.c0;
+        float4 at[6];
+        stencil_quad(g, t, ie, sig2, qd, at);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const float4 tv = ld4(t + c * nc + c0);
+          x[c] = make_float4(sp * tv.x, sp * tv.y, sp * tv.z, sp * tv.w);
+          y[c] = make_float4(sp * at[c].x - hjj * x[c].x, sp * at[c].y - hjj * x[c].y, sp * at[c].z - hjj * x[c].z,
+                             sp * at[c].w - hjj * x[c].w);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) x[c] = y[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    const int b = (int)(e % SW_STAGES);
+    if (ok) ok = mbar_wait(&full[b], (unsigned)((e / SW_STAGES) & 1));
+    float pa = 0.f, pb = 0.f;
+    if (act) {
+      // an inactive thread reads no buffer (the tile's tail is not copied)
+      const float* sb = ring + b * SW_STAGE_FLOATS + 4 * threadIdx.x;
+      float4 vv[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) vv[c] = *reinterpret_cast<const float4*>(sb + c * SW_TILE);
+      float2 sa = make_float2(0.f, 0.f), sx = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        sa = __ffma2_rn(lo2(vv[c]), lo2(y[c]), sa);
+        sa = __ffma2_rn(hi2(vv[c]), hi2(y[c]), sa);
+        sx = __ffma2_rn(lo2(vv[c]), lo2(x[c]), sx);
+        sx = __ffma2_rn(hi2(vv[c]), hi2(x[c]), sx);
+      }
+      pa = sa.x + sa.y;
+      pb = sx.x + sx.y;
+      const float2 na = make_float2(-ch[col], -ch[col]), nb = make_float2(-cc[col], -cc[col]);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        x[c] = join2(__ffma2_rn(na, lo2(vv[c]), lo2(x[c])), __ffma2_rn(na, hi2(vv[c]), hi2(x[c])));
+        y[c] = join2(__ffma2_rn(nb, lo2(vv[c]), lo2(y[c])), __ffma2_rn(nb, hi2(vv[c]), hi2(y[c])));
+      }
+    }
+    const float r = warp_sum2(pa, pb, lane);
+    if ((lane & 15) == 0) acc[warp][(lane >> 4) * j + col] += (double)r;
+    if (col == j - 1) {
+      // the tile ends: store V_j = x, accumulate x.x, x.y, y.y
+      float xx = 0.f, xy = 0.f, yy = 0.f;
+      if (act) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          *reinterpret_cast<float4*>(xout + c * nc + c0) = x[c];
+          xx += dot4(x[c], x[c]);
+          xy += dot4(x[c], y[c]);
+          yy += dot4(y[c], y[c]);
+        }
+      }
+      xx = warp_sum(xx);
+      xy = warp_sum(xy);
+      yy = warp_sum(yy);
+      if (lane == 0) {
+        acc[warp][2 * j] += (double)xx;
+        acc[warp][2 * j + 1] += (double)xy;
+        acc[warp][2 * j + 2] += (double)yy;
+      }
+    }
+    // every thread is done with buffer b: refill it with element e + SW_STAGES
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) {
+        s.st->status = KX_ETIMEOUT;
+        s.st->done = 1;
+        for (int64_t f = e; f < E && f < e + SW_STAGES; ++f)
+          mbar_wait(&full[f % SW_STAGES], (unsigned)((f / SW_STAGES) & 1));
+      }
+      return;
+    }
+    if (threadIdx.x == 0 && e + SW_STAGES < E) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      sw_issue(s, ld, nc, j, e + SW_STAGES, ring, full);
+    }
+    if (++col == j) {
+      col = 0;
+      tile += gridDim.x;
+    }
+  }
+  pdl_trigger();
+  __syncthreads();
+  for (int c2 = threadIdx.x; c2 < 2 * j + 3; c2 += blockDim.x) {
     double tsum = 0.0;
 #pragma unroll
-    for (int q = 0; q < NWARPS; ++q) tsum += acc[q][col];
-    w.part[(int64_t)col * w.ps + blockIdx.x] = tsum;
+    for (int q = 0; q < NWARPS; ++q) tsum += acc[q][c2];
+    w.part[(int64_t)c2 * w.ps + blockIdx.x] = tsum;
   }
 }
 
@@ -572,7 +675,7 @@ __global__ void __launch_bounds__(NTHREADS, SW_MINB4) k_sw_pass4(Geo g, Slot<flo
 // m_done = m and the breakdown test.
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS) k_sw_last(Slot<T> s, SwSlot w, int m, int ldh, int nbs, double btol) {
-  pdl_enter();
+  pdl_wait();
   if (s.st->done || s.st->retired) return;
   const double x = block_column_sum(w.part, w.ps, 2 * m, nbs);
   if (threadIdx.x == 0) w.co->tot[2 * m] = x;
@@ -597,11 +700,11 @@ static SwSlot sw_slot(kx_ctx* c, int slot) {
 
 // Persistent grids (occupancy x SMs, capped by the work and the partial
 // stride), shrunk for resident CTAs of kernels running beside the process.
-static void sw_grids(kx_ctx* c, const void* fa, const void* fs, int kind, int64_t items, int* nb_apply,
-                     int* nb_sweep) {
+static void sw_grids(kx_ctx* c, const void* fa, const void* fs, size_t smem_s, int kind, int64_t items,
+                     int* nb_apply, int* nb_sweep) {
   static std::atomic<int> ga[8], gs[8];
   if (!ga[kind]) ga[kind] = persistent_grid(c, fa, 1 << 30, 0);
-  if (!gs[kind]) gs[kind] = persistent_grid(c, fs, 1 << 30, 0);
+  if (!gs[kind]) gs[kind] = persistent_grid(c, fs, 1 << 30, smem_s);
   const int64_t rounds = (items + NTHREADS - 1) / NTHREADS;
   *nb_apply = reserve_grid(c, (int)std::min<int64_t>(rounds, ga[kind].load()), ga[kind].load());
   *nb_sweep = reserve_grid(c, (int)std::min<int64_t>(rounds, gs[kind].load()), gs[kind].load());
@@ -621,11 +724,15 @@ static kx_status sweep_t(kx_ctx* c, int slot, int m) {
   constexpr bool f3 = sizeof(T) == 4 && DIM == 3;
   const bool quad = f3 && (g.nx % 4) == 0;
   int nba = 0, nbs = 0;
-  if (quad)
-    sw_grids(c, (const void*)k_sw_apply4, (const void*)k_sw_pass4, 7, g.ncell / 4, &nba, &nbs);
-  else
-    sw_grids(c, (const void*)k_sw_apply<T, DIM, TableMat<T>>, (const void*)k_sw_pass<T, DIM, TableMat<T>>,
+  if (quad) {
+    static std::atomic<int> smem_set{0};
+    if (!smem_set.exchange(1))
+      cudaFuncSetAttribute(k_sw_pass4s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SW_SMEM);
+    sw_grids(c, (const void*)k_sw_apply4, (const void*)k_sw_pass4s, SW_SMEM, 7, g.ncell / 4, &nba, &nbs);
+  } else {
+    sw_grids(c, (const void*)k_sw_apply<T, DIM, TableMat<T>>, (const void*)k_sw_pass<T, DIM, TableMat<T>>, 0,
              (sizeof(T) == 8 ? 3 : 0) + (DIM - 2), g.ncell, &nba, &nbs);
+  }
   const double vb = (double)c->n * c->esize;
   const double mb = (double)g.ne * g.ncell * c->esize;
   for (int j = 0; j <= m; ++j) {
@@ -633,7 +740,7 @@ static kx_status sweep_t(kx_ctx* c, int slot, int m) {
       time_begin(c);
       if constexpr (f3) {
         if (quad)
-          launch_k(c, k_sw_pass4, dim3(nbs), dim3(NTHREADS), 0, c->stream, g, (Slot<float>)s, w, j, c->ld,
+          launch_k(c, k_sw_pass4s, dim3(nbs), dim3(NTHREADS), SW_SMEM, c->stream, g, (Slot<float>)s, w, j, c->ld,
                    (const float*)ie, (const float*)sg);
         else
           launch_k(c, k_sw_pass<T, DIM, TableMat<T>>, dim3(nbs), dim3(NTHREADS), 0, c->stream, g, s, w, j, c->ld,

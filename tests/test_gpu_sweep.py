@@ -152,7 +152,7 @@ def test_restart_dim_forms_agree(prec, tol, nx):
     T = 20.0
     dt = torch.float64 if prec == "fp64" else torch.float32
     Y = {}
-    for form in ("twopass", "default"):
+    for form in ("twopass", "sweep"):
         ctx = Context(grid, eps, precision=prec, krylov_dim=24, max_freqs=3, batch=2, rst_samples=8000,
                       arnoldi=form)
         out = ctx.response_restart_dim(dev(g, dt), oms, T, rtol=1e-11 if prec == "fp64" else 1e-7, plane=(2, 9),
@@ -162,5 +162,5 @@ def test_restart_dim_forms_agree(prec, tol, nx):
     A = yee.Operator(grid, eps).matrix()
     for f, W in enumerate(oms):
         want = exact.y_plain(A, g, W, T)
-        assert rel(Y["default"][f], want) < (1e-9 if prec == "fp64" else 3e-6)
-        assert rel(Y["default"][f], Y["twopass"][f]) < tol
+        assert rel(Y["sweep"][f], want) < (1e-9 if prec == "fp64" else 3e-6)
+        assert rel(Y["sweep"][f], Y["twopass"][f]) < tol
