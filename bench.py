@@ -30,11 +30,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "freq responses/s at 1e-6 rel err vs per-freq Krylov; A·v+GS HBM GB/s"
 
-# DRAM bytes / algorithmic bytes per launch of the two Arnoldi kernels, from
-# the ncu captures summarised in profiles/rstdim_3d128_32f_ncu.md (single
-# basis, step j = 60, 96^3; the ratio carries over to other sizes).  Set to
-# None whenever those kernels change.
-NCU_TRAFFIC_RATIO = {"k_pass_a": 1.014, "k_pass_b": 1.000}
+# DRAM bytes / algorithmic bytes per launch of the Arnoldi kernels, from the
+# ncu captures summarised in profiles/rstdim_3d128_32f_ncu.md (two-pass form)
+# and profiles/sweep_3d128_32f_ncu.md (single sweep): single basis, step
+# j = 60, 96^3; the ratio carries over to other sizes.  Set to None whenever
+# those kernels change.
+NCU_TRAFFIC_RATIO = {"k_pass_a": 1.014, "k_pass_b": 1.000, "k_sw_pass": 0.999}
 
 WORKLOADS = {
     # 3D Yee 64^3, random eps=2.25 spheres (fill 0.3, r 2-5), 8-cell layer,
