@@ -314,4 +314,33 @@ __device__ __forceinline__ void stencil_quad(const Geo& g, const float* __restri
   }
 }
 
+// L2 prefetch of the lines stencil_quad reads for a quad (its own six
+// components, the y and z neighbours it uses, the three 1/eps rows): issued
+// one quad (or tile) ahead, it lets a latency-bound loop keep the next
+// round's DRAM traffic in flight.  q must be a quad of the grid.
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+__device__ __forceinline__ void prefetch_quad(const Geo& g, const float* v, const float* ie, const Quad& q) {
+  const int64_t nc = g.ncell;
+  const int64_t nxy = (int64_t)g.nx * g.ny;
+  const int64_t c0 = q.c0;
+  const int jj = q.jj, kk = q.kk;
+  const int jp = (jj + 1 == g.ny) ? 0 : jj + 1, jm = (jj == 0) ? g.ny - 1 : jj - 1;
+  const int kp = (kk + 1 == g.nz) ? 0 : kk + 1, km = (kk == 0) ? g.nz - 1 : kk - 1;
+  const int64_t cjp = c0 + (int64_t)(jp - jj) * g.nx, cjm = c0 + (int64_t)(jm - jj) * g.nx;
+  const int64_t ckp = c0 + (int64_t)(kp - kk) * nxy, ckm = c0 + (int64_t)(km - kk) * nxy;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) prefetch_l2(v + c * nc + c0);
+  prefetch_l2(v + 5 * nc + cjp);
+  prefetch_l2(v + 3 * nc + cjp);
+  prefetch_l2(v + 4 * nc + ckp);
+  prefetch_l2(v + 3 * nc + ckp);
+  prefetch_l2(v + 2 * nc + cjm);
+  prefetch_l2(v + cjm);
+  prefetch_l2(v + nc + ckm);
+  prefetch_l2(v + ckm);
+#pragma unroll
+  for (int e = 0; e < 3; ++e) prefetch_l2(ie + e * nc + c0);
+}
+
 }  // namespace kx

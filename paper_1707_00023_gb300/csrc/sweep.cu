@@ -44,6 +44,7 @@ namespace kx {
 namespace {
 
 constexpr int LG = MMAX + 1;   // leading dimension of the Gram matrix
+static_assert(NTHREADS >= SWCOLS, "the finalisation stages one reduced column a thread");
 
 // Sum over the four lanes of a row group (lanes 4r .. 4r+3) in a fixed order.
 __device__ __forceinline__ double quad_sum(double x) {
@@ -91,19 +92,37 @@ __device__ void sw_fin(const Slot<T>& s, SwCoef* co, double* G, int j, int ldh, 
     }
     return;
   }
+  // every load first (one L2 round trip), then the shared-memory stores;
+  // blockDim.x == NTHREADS >= SWCOLS, so one reduced column a thread
   const bool full = !final_step;
-  for (int q = tid; q < 2 * j + 3; q += blockDim.x) sh_tot[q] = __ldcg(&co->tot[q]);
-  if (full) {
-    for (int q = tid; q < j; q += blockDim.x) {
-      sh_u[0][q] = __ldcg(&co->uh[q]);
-      sh_u[1][q] = __ldcg(&co->uc[q]);
-      sh_sc[q] = s.scale[q];
-    }
-    // H(k, i), k <= j, i < j, nonzero for i >= k - 1 (H(j, j-1) is set below)
-    for (int q = tid; q < (j + 1) * j; q += blockDim.x) {
-      const int k = q % (j + 1), i = q / (j + 1);
-      sh_H[k + i * LG] = (i >= k - 1 && k < j) ? s.H[k + (int64_t)i * ldh] : 0.0;
-    }
+  constexpr int HPER = (LG * MMAX + NTHREADS - 1) / NTHREADS;   // H entries a thread
+  const int nh = full ? (j + 1) * j : 0;
+  const double tv = tid < 2 * j + 3 ? __ldcg(&co->tot[tid]) : 0.0;
+  double uv = 0.0, cv0 = 0.0, sv = 0.0, wm = 0.0;
+  if (full && tid < j) {
+    uv = __ldcg(&co->uh[tid]);
+    cv0 = __ldcg(&co->uc[tid]);
+    sv = s.scale[tid];
+  }
+  if (tid == 0) wm = st->wmax;
+  // H(k, i), k <= j, i < j, nonzero for i >= k - 1 (H(j, j-1) is set below)
+  double hv[HPER];
+#pragma unroll
+  for (int r = 0; r < HPER; ++r) {
+    const int q = tid + r * NTHREADS;
+    const int k = q % (j + 1), i = q / (j + 1);
+    hv[r] = (q < nh && i >= k - 1 && k < j) ? s.H[k + (int64_t)i * ldh] : 0.0;
+  }
+  if (tid < 2 * j + 3) sh_tot[tid] = tv;
+  if (full && tid < j) {
+    sh_u[0][tid] = uv;
+    sh_u[1][tid] = cv0;
+    sh_sc[tid] = sv;
+  }
+#pragma unroll
+  for (int r = 0; r < HPER; ++r) {
+    const int q = tid + r * NTHREADS;
+    if (q < nh) sh_H[(q % (j + 1)) + (q / (j + 1)) * LG] = hv[r];
   }
   __syncthreads();
   if (tid == 0) {
@@ -111,7 +130,7 @@ __device__ void sw_fin(const Slot<T>& s, SwCoef* co, double* G, int j, int ldh, 
     int stop = 0;
     double sig = 0.0;
     if (!isfinite(b)) stop = 2;
-    else if (b <= btol * st->wmax) stop = 1;   // invariant subspace: the projection is exact
+    else if (b <= btol * wm) stop = 1;   // invariant subspace: the projection is exact
     else sig = 1.0 / b;
     s.H[j + (int64_t)(j - 1) * ldh] = b;
     s.scale[j] = sig;
@@ -141,7 +160,7 @@ __device__ void sw_fin(const Slot<T>& s, SwCoef* co, double* G, int j, int ldh, 
     if (!isfinite(an)) {
       st->status = KX_ENONFINITE;
       st->done = 1;
-    } else if (an > st->wmax) {
+    } else if (an > wm) {
       st->wmax = an;
     }
   }
@@ -203,22 +222,27 @@ __device__ __forceinline__ bool last_of(unsigned* counter, unsigned count) {
   return am_last;
 }
 
-// Step j >= 1, at the start of apply pass K_j: the first R = min(grid,
-// 2j+3) blocks reduce sweep S_j's partial columns (one column a block) and
-// form the Gram-row products uh, uc of rows i < j (one warp a row); the last
-// of them finalises step j.  This runs beside the other blocks' stencil
-// work, which reads none of it.
+// Step j >= 1, in the SW_RED blocks at the front of apply pass K_j, which
+// do no stencil work: sweep S_j's partial columns reduced (one warp a
+// column, its lanes over the sweep's blocks in a fixed order) and the
+// Gram-row products uh, uc of rows i < j (one warp a row); the last of these
+// blocks finalises step j.  The stencil blocks behind them read none of it,
+// so the finalisation runs beside the stencil instead of after it.
+constexpr int SW_RED = 16;
 template <typename T>
-__device__ __forceinline__ void sw_apply_head(const Slot<T>& s, const SwSlot& w, int j, int ldh, int nbs,
+__device__ __forceinline__ void sw_reduce_fin(const Slot<T>& s, const SwSlot& w, int j, int ldh, int nbs,
                                               double btol) {
-  const int R = min((int)gridDim.x, 2 * j + 3);
-  if ((int)blockIdx.x >= R) return;
-  for (int col = blockIdx.x; col < 2 * j + 3; col += R) {
-    const double x = block_column_sum(w.part, w.ps, col, nbs);
-    if (threadIdx.x == 0) w.co->tot[col] = x;
-  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int row = blockIdx.x * NWARPS + warp; row < j; row += R * NWARPS) {
+  const int gw = blockIdx.x * NWARPS + warp;
+  for (int col = gw; col < 2 * j + 3; col += SW_RED * NWARPS) {
+    const double* p = w.part + (int64_t)col * w.ps;
+    double x = 0.0;
+#pragma unroll 4
+    for (int b = lane; b < nbs; b += 32) x += __ldcg(p + b);
+    x = warp_sum(x);
+    if (lane == 0) w.co->tot[col] = x;
+  }
+  for (int row = gw; row < j; row += SW_RED * NWARPS) {
     double uh = 0.0, uc = 0.0;
     for (int l = row + lane; l < j; l += 32) {
       const double gil = w.G[row + (int64_t)l * LG];
@@ -232,7 +256,7 @@ __device__ __forceinline__ void sw_apply_head(const Slot<T>& s, const SwSlot& w,
       w.co->uc[row] = uc;
     }
   }
-  if (!last_of(&w.co->counter, (unsigned)R)) return;
+  if (!last_of(&w.co->counter, (unsigned)SW_RED)) return;
   sw_fin<T>(s, w.co, w.G, j, ldh, btol, 0);
   if (threadIdx.x == 0) w.co->counter = 0u;
 }
@@ -254,21 +278,26 @@ __device__ __forceinline__ void sw_apply_tail0(const Slot<T>& s, const SwSlot& w
   if (threadIdx.x == 0) w.co->counter = 0u;
 }
 
-// Apply pass K_j, any model and precision, one cell a thread: t = A V_j
-// (with step j's finalisation beside it, or step 0's after it).
+// Apply pass K_j, any model and precision, one cell a thread: t = A V_j.
+// Steps j >= 1 launch SW_RED more blocks in front, which finalise step j
+// beside the stencil; step 0's finalisation follows its stencil.
 template <typename T, int DIM, typename Mat>
 __global__ void __launch_bounds__(NTHREADS) k_sw_apply(Geo g, Slot<T> s, SwSlot w, int j, int64_t ld, Mat mat,
                                                       int ldh, int nbs, double btol) {
   pdl_wait();
   if (s.st->done || s.st->retired) return;
   constexpr int NC = ncomp_of(DIM);
-  if (j >= 1) sw_apply_head<T>(s, w, j, ldh, nbs, btol);
+  const int R = j >= 1 ? SW_RED : 0;
+  if ((int)blockIdx.x < R) {
+    sw_reduce_fin<T>(s, w, j, ldh, nbs, btol);
+    return;
+  }
   const T* __restrict__ v = s.V + (int64_t)j * ld;
   T* __restrict__ t = (T*)w.t;
   const int64_t nc = g.ncell;
   double d0 = 0.0, d1 = 0.0;
-  for (int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cell < nc;
-       cell += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t cell = (int64_t)(blockIdx.x - R) * blockDim.x + threadIdx.x; cell < nc;
+       cell += (int64_t)(gridDim.x - R) * blockDim.x) {
     const Cell q = make_cell(g, cell);
     T o[NC];
     stencil<T, DIM, 0>(g, v, mat, q, o);
@@ -290,17 +319,25 @@ __global__ void __launch_bounds__(NTHREADS) k_sw_apply(Geo g, Slot<T> s, SwSlot 
 }
 
 // Apply pass K_j, 3D FP32, one quad of x-cells a thread (nx % 4 == 0).
-__global__ void __launch_bounds__(NTHREADS) k_sw_apply4(Geo g, Slot<float> s, SwSlot w, int j, int64_t ld,
+// Three resident blocks per SM (80 registers, a small spill): the stencil is
+// latency-bound, and against two blocks (128 registers) the apply pass took
+// 77 instead of 97 ms a step at 128^3 and 41.5 instead of 49 at 96^3.
+__global__ void __launch_bounds__(NTHREADS, 3) k_sw_apply4(Geo g, Slot<float> s, SwSlot w, int j, int64_t ld,
                                                        const float* __restrict__ ie, const float* __restrict__ sig2,
                                                        int ldh, int nbs, double btol) {
   pdl_wait();
   if (s.st->done || s.st->retired) return;
-  if (j >= 1) sw_apply_head<float>(s, w, j, ldh, nbs, btol);
+  const int R = j >= 1 ? SW_RED : 0;
+  if ((int)blockIdx.x < R) {
+    sw_reduce_fin<float>(s, w, j, ldh, nbs, btol);
+    return;
+  }
   const float* __restrict__ v = s.V + (int64_t)j * ld;
   float* __restrict__ t = (float*)w.t;
   const int64_t nc = g.ncell, nq = nc >> 2;
   double d0 = 0.0, d1 = 0.0;
-  for (int64_t q4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q4 < nq; q4 += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t q4 = (int64_t)(blockIdx.x - R) * blockDim.x + threadIdx.x; q4 < nq;
+       q4 += (int64_t)(gridDim.x - R) * blockDim.x) {
     const Quad qd = make_quad(g, q4);
     float4 o[6];
     stencil_quad(g, v, ie, sig2, qd, o);
@@ -480,10 +517,11 @@ __device__ __forceinline__ float warp_sum2(float v0, float v1, int lane) {
 // Every wait is bounded: when one runs out the block records KX_ETIMEOUT,
 // waits (bounded again) for its own copies and returns.
 constexpr int SW_TILE = 4 * NTHREADS;                             // cells a tile
-constexpr int SW_STAGES = 4;                                      // buffers in the ring
+constexpr int SW_STAGES = 4;                                      // buffers in the ring (a power of 2)
 constexpr size_t SW_STAGE_FLOATS = 6 * (size_t)SW_TILE;           // one column of a tile
 constexpr size_t SW_SMEM = SW_STAGES * SW_STAGE_FLOATS * sizeof(float);
 constexpr unsigned SW_WAIT_LIMIT = 1u << 22;                      // try_wait rounds of one wait
+static_assert(SW_STAGES == 4, "the wait parity below is (e >> 2) & 1");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -516,24 +554,36 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
                : "memory");
 }
 
-// Element e of a block's stream: column e % j of its tile e / j, into
-// buffer e % SW_STAGES (16-byte aligned: tiles start at multiples of 1024
-// cells, columns at multiples of 64 scalars, components at multiples of
-// ncell with ncell % 4 == 0; each copy is a multiple of 16 bytes).
-__device__ __forceinline__ void sw_issue(const Slot<float>& s, int64_t ld, int64_t nc, int j, int64_t e, float* ring,
-                                         uint64_t* full) {
-  const int64_t tile = blockIdx.x + (e / j) * gridDim.x;
-  const int col = (int)(e % j);
+// Element e of a block's stream: column `col` of tile `tile` (e = its
+// index in the block's (tile, column) order), into buffer e % SW_STAGES
+// (16-byte aligned: tiles start at multiples of 1024 cells, columns at
+// multiples of 64 scalars, components at multiples of ncell with
+// ncell % 4 == 0; each copy is a multiple of 16 bytes).
+__device__ __forceinline__ void sw_issue(const Slot<float>& s, int64_t ld, int64_t nc, int64_t tile, int col, int b,
+                                         float* ring, uint64_t* full) {
   const int64_t cell0 = tile * SW_TILE;
   const int64_t cells = nc - cell0 < SW_TILE ? nc - cell0 : SW_TILE;
   const unsigned bytes = (unsigned)(cells * (int64_t)sizeof(float));
-  const int b = (int)(e % SW_STAGES);
   float* dst = ring + b * SW_STAGE_FLOATS;
   const float* src = s.V + (int64_t)col * ld + cell0;
   mbar_expect_tx(&full[b], 6u * bytes);
 #pragma unroll
   for (int c = 0; c < 6; ++c) bulk_load(dst + c * SW_TILE, src + c * nc, bytes, &full[b]);
 }
+
+// The issue cursor of a block's stream (thread 0 only): advancing it by one
+// element moves to the next column, or to the first column of the block's
+// next tile (no division in the loop).
+struct SwCursor {
+  int64_t tile;
+  int col;
+  __device__ __forceinline__ void next(int j) {
+    if (++col == j) {
+      col = 0;
+      tile += gridDim.x;
+    }
+  }
+};
 
 __global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s, SwSlot w, int j, int64_t ld,
                                                           const float* __restrict__ ie,
@@ -562,8 +612,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s,
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  SwCursor cur{(int64_t)blockIdx.x, 0};   // the next element to issue (thread 0)
   if (threadIdx.x == 0)
-    for (int64_t e = 0; e < E && e < SW_STAGES; ++e) sw_issue(s, ld, nc, j, e, ring, full);
+    for (int64_t e = 0; e < E && e < SW_STAGES; ++e) {
+      sw_issue(s, ld, nc, cur.tile, cur.col, (int)e, ring, full);
+      cur.next(j);
+    }
   const float* __restrict__ t = (const float*)w.t;
   float* __restrict__ xout = s.V + (int64_t)j * ld;
   float4 x[6], y[6];
@@ -593,8 +647,13 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s,
         for (int c = 0; c < 6; ++c) x[c] = y[c] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
-    const int b = (int)(e % SW_STAGES);
-    if (ok) ok = mbar_wait(&full[b], (unsigned)((e / SW_STAGES) & 1));
+    if (col == j - 1) {
+      // the tile's last column: prefetch the next tile's stencil inputs
+      const int64_t qn = (tile + gridDim.x) * NTHREADS + threadIdx.x;
+      if (qn < nq) prefetch_quad(g, t, ie, make_quad(g, qn));
+    }
+    const int b = (int)(e & (SW_STAGES - 1));
+    if (ok) ok = mbar_wait(&full[b], (unsigned)((e >> 2) & 1));
     float pa = 0.f, pb = 0.f;
     if (act) {
       // an inactive thread reads no buffer (the tile's tail is not copied)
@@ -602,16 +661,17 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s,
       float4 vv[6];
 #pragma unroll
       for (int c = 0; c < 6; ++c) vv[c] = *reinterpret_cast<const float4*>(sb + c * SW_TILE);
-      float2 sa = make_float2(0.f, 0.f), sx = make_float2(0.f, 0.f);
+      // two independent accumulator chains per dot (the quad's two halves)
+      float2 sa = make_float2(0.f, 0.f), sa2 = sa, sx = sa, sx2 = sa;
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
         sa = __ffma2_rn(lo2(vv[c]), lo2(y[c]), sa);
-        sa = __ffma2_rn(hi2(vv[c]), hi2(y[c]), sa);
+        sa2 = __ffma2_rn(hi2(vv[c]), hi2(y[c]), sa2);
         sx = __ffma2_rn(lo2(vv[c]), lo2(x[c]), sx);
-        sx = __ffma2_rn(hi2(vv[c]), hi2(x[c]), sx);
+        sx2 = __ffma2_rn(hi2(vv[c]), hi2(x[c]), sx2);
       }
-      pa = sa.x + sa.y;
-      pb = sx.x + sx.y;
+      pa = (sa.x + sa2.x) + (sa.y + sa2.y);
+      pb = (sx.x + sx2.x) + (sx.y + sx2.y);
       const float2 na = make_float2(-ch[col], -ch[col]), nb = make_float2(-cc[col], -cc[col]);
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
@@ -648,13 +708,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s,
         s.st->status = KX_ETIMEOUT;
         s.st->done = 1;
         for (int64_t f = e; f < E && f < e + SW_STAGES; ++f)
-          mbar_wait(&full[f % SW_STAGES], (unsigned)((f / SW_STAGES) & 1));
+          mbar_wait(&full[f & (SW_STAGES - 1)], (unsigned)((f >> 2) & 1));
       }
       return;
     }
     if (threadIdx.x == 0 && e + SW_STAGES < E) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      sw_issue(s, ld, nc, j, e + SW_STAGES, ring, full);
+      sw_issue(s, ld, nc, cur.tile, cur.col, b, ring, full);
+      cur.next(j);
     }
     if (++col == j) {
       col = 0;
@@ -751,18 +812,21 @@ static kx_status sweep_t(kx_ctx* c, int slot, int m) {
       time_end(c, KX_K_SWEEP, (j + 2.0) * vb + mb);
       KX_CHECK_LAUNCH(c);
     }
+    // the apply grid: the stencil blocks (shrunk by the reducer blocks when
+    // that keeps every block resident) and, from step 1, SW_RED in front
+    const int ga = j == 0 ? nba : (nba > 2 * SW_RED ? nba - SW_RED : nba) + SW_RED;
     time_begin(c);
     if (j == m) {
       launch_k(c, k_sw_last<T>, dim3(1), dim3(NTHREADS), 0, c->stream, s, w, m, ldh, nbs, bt);
     } else if constexpr (f3) {
       if (quad)
-        launch_k(c, k_sw_apply4, dim3(nba), dim3(NTHREADS), 0, c->stream, g, (Slot<float>)s, w, j, c->ld,
+        launch_k(c, k_sw_apply4, dim3(ga), dim3(NTHREADS), 0, c->stream, g, (Slot<float>)s, w, j, c->ld,
                  (const float*)ie, (const float*)sg, ldh, nbs, bt);
       else
-        launch_k(c, k_sw_apply<T, DIM, TableMat<T>>, dim3(nba), dim3(NTHREADS), 0, c->stream, g, s, w, j, c->ld, mat,
+        launch_k(c, k_sw_apply<T, DIM, TableMat<T>>, dim3(ga), dim3(NTHREADS), 0, c->stream, g, s, w, j, c->ld, mat,
                  ldh, nbs, bt);
     } else {
-      launch_k(c, k_sw_apply<T, DIM, TableMat<T>>, dim3(nba), dim3(NTHREADS), 0, c->stream, g, s, w, j, c->ld, mat,
+      launch_k(c, k_sw_apply<T, DIM, TableMat<T>>, dim3(ga), dim3(NTHREADS), 0, c->stream, g, s, w, j, c->ld, mat,
                ldh, nbs, bt);
     }
     time_end(c, KX_K_SWAPPLY, j < m ? 2.0 * vb + mb : 0.0);
