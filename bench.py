@@ -35,7 +35,7 @@ METRIC = "freq responses/s at 1e-6 rel err vs per-freq Krylov; A·v+GS HBM GB/s"
 # and profiles/sweep_3d128_32f_ncu.md (single sweep): single basis, step
 # j = 60, 96^3; the ratio carries over to other sizes.  Set to None whenever
 # those kernels change.
-NCU_TRAFFIC_RATIO = {"k_pass_a": 1.014, "k_pass_b": 1.000, "k_sw_pass": 0.999}
+NCU_TRAFFIC_RATIO = {"k_pass_a": 1.014, "k_pass_b": 1.000, "k_sw_pass": 1.000}
 
 WORKLOADS = {
     # 3D Yee 64^3, random eps=2.25 spheres (fill 0.3, r 2-5), 8-cell layer,
