@@ -346,6 +346,16 @@ kx_status kx_kernel_times(kx_ctx* ctx, kx_kernel_time out[KX_NKCLASS]);
  * the last creation failure of the calling thread. */
 const char* kx_last_error(const kx_ctx* ctx);
 
+/* Check of the device-side failure path (not a paper operation): every wait
+ * in this library's kernels is bounded (the single-sweep Arnoldi waits on
+ * mbarriers for its basis copies); when a wait runs out the kernel records
+ * KX_ETIMEOUT, returns normally and the context stays usable.  This call
+ * runs that wait, `rounds` try_wait rounds (>= 1), on an mbarrier that
+ * nothing completes and no copy targets.  Synchronises the stream.
+ * Returns KX_ETIMEOUT (the expected outcome), KX_EINVAL (rounds == 0) or
+ * KX_ECUDA. */
+kx_status kx_wait_selftest(kx_ctx* ctx, unsigned rounds);
+
 /* Allocation-free Arnoldi (the paper has no counterpart: this is a
  * deployment convenience).  Some callers cannot allocate device memory at
  * all -- code running inside another runtime's memory pool or a captured

@@ -29,7 +29,7 @@ EXPORTS = ["krylov_expm_create", "krylov_expm_destroy", "kx_num_unknowns", "appl
            "response_at_freqs", "kx_get_stats", "kx_reset_stats", "kx_set_timing",
            "kx_kernel_times", "kx_last_error", "kx_arnoldi_noalloc", "kx_noalloc_last_error",
            "adjoint_response_grad", "kx_set_permittivity", "response_at_freqs_multi", "kx_stream",
-           "response_restart_dim"]
+           "response_restart_dim", "kx_wait_selftest"]
 KCLASSES = ["pass_a", "pass_b", "restart", "projected", "zupdate", "apply", "cascade", "sweep", "swapply"]
 # Arnoldi forms (kx_desc.arnoldi_form)
 ARNOLDI_FORMS = {"default": 0, "twopass": 1, "sweep": 2}
@@ -104,6 +104,7 @@ def load_library(path: Optional[str] = None):
     lib.kx_last_error.restype = ctypes.c_char_p
     lib.kx_arnoldi_noalloc.argtypes = [ctypes.POINTER(Desc), vp, vp, ctypes.c_int, vp, vp, dp, ip, vp]
     lib.kx_noalloc_last_error.argtypes = []
+    lib.kx_wait_selftest.argtypes = [vp, ctypes.c_uint]
     lib.kx_noalloc_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name not in ("kx_num_unknowns", "kx_last_error", "kx_noalloc_last_error", "kx_stream"):
@@ -213,6 +214,11 @@ class Context:
 
     def set_timing(self, on: bool):
         self._check(self.lib.kx_set_timing(self.h, int(bool(on))))
+
+    def wait_selftest(self, rounds: int = 1000) -> int:
+        """Run the library's bounded device wait on an mbarrier nothing
+        completes; returns the status (KX_ETIMEOUT expected), no raise."""
+        return int(self.lib.kx_wait_selftest(self.h, rounds))
 
     def kernel_times(self):
         """Per-class {ms, bytes, launches} recorded since timing was switched on."""

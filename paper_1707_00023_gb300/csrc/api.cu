@@ -1304,6 +1304,20 @@ void time_end(kx_ctx* c, int cls, double bytes) {
 
 extern "C" {
 
+kx_status kx_wait_selftest(kx_ctx* c, unsigned rounds) {
+  if (!c) return KX_EINVAL;
+  if (rounds == 0) return fail(c, KX_EINVAL, "rounds must be >= 1");
+  int* d_status = reinterpret_cast<int*>(c->d_small + 200);
+  KX_CUDA(c, cudaMemsetAsync(d_status, 0xff, sizeof(int), c->stream), "status reset");
+  KX_TRY(launch_wait_selftest(c, rounds, d_status));
+  int h = -1;
+  KX_CUDA(c, cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status read");
+  KX_TRY(sync(c));
+  if (h == KX_ETIMEOUT) return fail(c, KX_ETIMEOUT, "bounded device wait ran out (self-test)");
+  if (h != KX_OK) return fail(c, KX_ECUDA, "self-test kernel did not report");
+  return KX_OK;
+}
+
 kx_status kx_set_timing(kx_ctx* c, int on) {
   if (!c) return KX_EINVAL;
   c->timing = on ? 1 : 0;

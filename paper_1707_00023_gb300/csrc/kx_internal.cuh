@@ -286,6 +286,8 @@ kx_status launch_rst_nextvec(kx_ctx* c, cudaStream_t st, int from, int to);
 // sweep.cu: m steps of the single-sweep Arnoldi process on basis slot
 // `slot`, from its column 0 as set by launch_norm_init (non-augmented)
 kx_status sweep_arnoldi(kx_ctx* c, int slot, int m);
+// the bounded mbarrier wait of the sweep on a barrier nothing completes
+kx_status launch_wait_selftest(kx_ctx* c, unsigned rounds, int* d_status);
 
 // projected.cu
 kx_status launch_substep_control(kx_ctx* c, int slot0, int ns);

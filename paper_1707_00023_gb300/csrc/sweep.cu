@@ -541,11 +541,27 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the completion of phase `parity` of b.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
-  for (unsigned k = 0; k < SW_WAIT_LIMIT; ++k)
+// Bounded wait for the completion of phase `parity` of b: false when
+// `limit` try_wait rounds pass without it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, unsigned limit = SW_WAIT_LIMIT) {
+  for (unsigned k = 0; k < limit; ++k)
     if (mbar_test(b, parity)) return true;
   return false;
+}
+
+// The failure path of that wait, checked without a fault: one warp waits on
+// an mbarrier that nothing completes (no copy is issued) and records
+// KX_ETIMEOUT when the wait runs out, as the sweep does.
+__global__ void k_wait_selftest(unsigned limit, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(&bar, 0u, limit);
+  if (threadIdx.x == 0) *status = __all_sync(0xffffffffu, ok) ? KX_OK : KX_ETIMEOUT;
+  else (void)__all_sync(0xffffffffu, ok);
 }
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* b) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -834,6 +850,12 @@ static kx_status sweep_t(kx_ctx* c, int slot, int m) {
   }
   c->stats.arnoldi_steps += m;
   c->stats.matvecs += 2 * (int64_t)m;
+  return KX_OK;
+}
+
+kx_status launch_wait_selftest(kx_ctx* c, unsigned rounds, int* d_status) {
+  k_wait_selftest<<<1, 32, 0, c->stream>>>(rounds, d_status);
+  KX_CHECK_LAUNCH(c);
   return KX_OK;
 }
 

@@ -164,3 +164,23 @@ def test_restart_dim_forms_agree(prec, tol, nx):
         want = exact.y_plain(A, g, W, T)
         assert rel(Y["sweep"][f], want) < (1e-9 if prec == "fp64" else 3e-6)
         assert rel(Y["sweep"][f], Y["twopass"][f]) < tol
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable():
+    """The failure path of the sweep's bounded mbarrier waits, without a
+    fault: a wait on a barrier that nothing completes runs out, the kernel
+    reports KX_ETIMEOUT and returns, and the context then computes as before."""
+    from paper_1707_00023_gb300 import _binding
+    grid = GRIDS["3d_quad"]
+    eps = eps_of(grid)
+    op = yee.Operator(grid, eps)
+    ctx = Context(grid, eps, precision="fp32", krylov_dim=16, arnoldi="sweep")
+    assert ctx.wait_selftest(1000) == _binding.KX_ETIMEOUT
+    assert b"ran out" in ctx.lib.kx_last_error(ctx.h)
+    v = S.masked_random_vector(grid, 9)
+    w = ctx.apply_A(dev(v, torch.float32)).double().cpu().numpy()
+    assert rel(w, op.apply(v)) < 1e-6
+    V, H, beta, md = ctx.arnoldi(dev(v, torch.float32), 16)
+    Vo, Ho, _, _ = krylov.arnoldi(op.apply, v, 16)
+    assert md == 16 and np.abs(H[:, :10] - Ho[:, :10]).max() < 1e-4 * np.abs(Ho).max()
+    ctx.close()
