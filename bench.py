@@ -531,7 +531,9 @@ def main():
                 "dtype": "f32" if w["prec"] == "fp32" else "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "grid": list(sc.grid.n), "unknowns": sc.grid.nunk,
                            "T": w["T"], "krylov_dim": w["m"], "nfreq": w["nfreq"], "method": w["method"],
-                           "projected": "f64", "arnoldi": args.arnoldi, "parallelism": f"replicas{world}",
+                           "projected": "f64", "arnoldi": args.arnoldi,
+                           "arnoldi_ran": "single sweep" if kt["sweep"]["launches"] else "two-pass",
+                           "parallelism": f"replicas{world}",
                            "l2": "working set (Krylov basis) larger than L2; no flush"},
                 "roofline": roofline,
                 "arnoldi_hbm_gbs": round(ab_gbs, 1),
