@@ -802,9 +802,13 @@ static kx_status sweep_t(kx_ctx* c, int slot, int m) {
   const bool quad = f3 && (g.nx % 4) == 0;
   int nba = 0, nbs = 0;
   if (quad) {
+    // the attribute is set before the flag, so no thread (contexts of the
+    // multi-problem driver run on several) launches before it is in place
     static std::atomic<int> smem_set{0};
-    if (!smem_set.exchange(1))
+    if (!smem_set.load()) {
       cudaFuncSetAttribute(k_sw_pass4s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SW_SMEM);
+      smem_set.store(1);
+    }
     sw_grids(c, (const void*)k_sw_apply4, (const void*)k_sw_pass4s, SW_SMEM, 7, g.ncell / 4, &nba, &nbs);
   } else {
     sw_grids(c, (const void*)k_sw_apply<T, DIM, TableMat<T>>, (const void*)k_sw_pass<T, DIM, TableMat<T>>, 0,
