@@ -207,13 +207,14 @@ def test_invalid_arguments_are_rejected():
     ctx.close()
 
 
-def test_multi_problem_driver_with_restart_in_dimension():
+@pytest.mark.parametrize("form", FORMS)
+def test_multi_problem_driver_with_restart_in_dimension(form):
     from paper_1707_00023_gb300 import response_multi
     scs = S.config_uneven(count=3, seed=6, nmin=8, nmax=12, T=15.0, m=24, nfreq=2)
     ctxs, gs = [], []
     for sc in scs:
         ctxs.append(Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=24, max_freqs=2,
-                            stream="own", rst_samples=4000))
+                            stream="own", rst_samples=4000, arnoldi=form))
         gs.append(dev(sc.g, "fp64"))
     torch.cuda.synchronize()
     oms = np.stack([sc.omegas for sc in scs])
@@ -223,6 +224,31 @@ def test_multi_problem_driver_with_restart_in_dimension():
         A = yee.Operator(sc.grid, sc.eps_cell).matrix()
         want = yee.intensity(sc.grid, exact.y_plain(A, sc.g, sc.omegas[0], 15.0), sc.plane)
         assert abs(inten[i, 0] - want) < 1e-9 * want
+    for c in ctxs:
+        c.close()
+
+
+def test_multi_problem_driver_single_sweep_fp32_threads():
+    """Three FP32 instances (16^3, 12^3, 16^3: the quad kernels of the single
+    sweep) solved at once from three host threads on private streams, each
+    against its exact response (plane intensity within 1e-5)."""
+    from paper_1707_00023_gb300 import response_multi
+    scs = S.config_uneven(count=3, seed=6, nmin=8, nmax=16, T=15.0, m=24, nfreq=2)
+    assert all(sc.grid.n[0] % 4 == 0 for sc in scs)
+    ctxs, gs = [], []
+    for sc in scs:
+        ctxs.append(Context(sc.grid, sc.eps_cell, precision="fp32", krylov_dim=24, max_freqs=2, batch=2,
+                            stream="own", rst_samples=4000, arnoldi="sweep"))
+        gs.append(dev(sc.g, "fp32"))
+    torch.cuda.synchronize()
+    oms = np.stack([sc.omegas for sc in scs])
+    planes = np.array([sc.plane for sc in scs])
+    inten, _ = response_multi(ctxs, gs, oms, 15.0, rtol=1e-7, method="rstdim", planes=planes, nthreads=3)
+    for i, sc in enumerate(scs):
+        A = yee.Operator(sc.grid, sc.eps_cell).matrix()
+        for f in range(2):
+            want = yee.intensity(sc.grid, exact.y_plain(A, sc.g, sc.omegas[f], 15.0), sc.plane)
+            assert abs(inten[i, f] - want) < 1e-5 * want
     for c in ctxs:
         c.close()
 
