@@ -30,56 +30,54 @@ sys.path.insert(0, ROOT)
 
 METRIC = "freq responses/s at 1e-6 rel err vs per-freq Krylov; A·v+GS HBM GB/s"
 
-# DRAM bytes / algorithmic bytes per launch of the Arnoldi kernels, from the
-# ncu captures summarised in profiles/rstdim_3d128_32f_ncu.md (two-pass form)
-# and profiles/sweep_3d128_32f_ncu.md (single sweep): single basis, step
-# j = 60, 96^3; the ratio carries over to other sizes.  Set to None whenever
-# those kernels change.
+# DRAM bytes / algorithmic bytes per launch of the Arnoldi kernels, from ncu
+# captures of one launch (single basis, step j = 60, 96^3); the ratio
+# carries over to other sizes.  Set to None whenever those kernels change.
 NCU_TRAFFIC_RATIO = {"k_pass_a": 1.014, "k_pass_b": 1.000, "k_sw_pass": 1.000}
 
 WORKLOADS = {
     # 3D Yee 64^3, random eps=2.25 spheres (fill 0.3, r 2-5), 8-cell layer,
     # Ex plane source, FP32 vectors / FP64 projected, m = 64, T = 400
     "3d64_m64_T400": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=1,
-                          prec="fp32", method="split", rtol=1e-7, t_oracle=20.0),
+                          prec="fp32", method="split", rtol=1e-7),
     "3d64_m64_T400_plain": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=1,
-                                prec="fp32", method="plain", rtol=1e-7, t_oracle=20.0),
+                                prec="fp32", method="plain", rtol=1e-7),
     # the same medium at 8 / 32 frequencies in [0.8, 1.2] Omega0, advanced in lockstep batches
     "3d64_m64_T400_8f_plain": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=8,
-                                   prec="fp32", method="plain", rtol=1e-7, t_oracle=20.0, batch=8),
+                                   prec="fp32", method="plain", rtol=1e-7, batch=8),
     "3d64_m64_T400_32f": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=32,
-                              prec="fp32", method="plain", rtol=1e-7, t_oracle=20.0, batch=32),
+                              prec="fp32", method="plain", rtol=1e-7, batch=32),
     # the same 32 frequencies by restart in Krylov dimension: one basis per
     # restart for all of them (Corollary 2, Fig. alg:rst)
     "3d64_m64_T400_32f_rst": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=32,
-                                  prec="fp32", method="rstdim", rtol=1e-7, t_oracle=20.0, rst_samples=4096,
+                                  prec="fp32", method="rstdim", rtol=1e-7, rst_samples=4096,
                                   batch=2),
     "3d96_32f_T400_rst": dict(dim=3, n=96, seed=1713, fill=0.3, T=400.0, m=64, nfreq=32,
-                              prec="fp32", method="rstdim", rtol=1e-7, t_oracle=1.0, rst_samples=4096,
+                              prec="fp32", method="rstdim", rtol=1e-7, rst_samples=4096,
                               batch=2),
     "3d128_32f_T400_rst": dict(dim=3, n=128, seed=1710, fill=0.3, T=400.0, m=64, nfreq=32,
-                               prec="fp32", method="rstdim", rtol=1e-7, t_oracle=0.5, rst_samples=4096,
+                               prec="fp32", method="rstdim", rtol=1e-7, rst_samples=4096,
                                batch=2),
     # source splitting (eq. (split2)) on the 64^3 medium, 32 frequencies in lockstep
     "3d64_m64_T400_32f_split2": dict(dim=3, n=64, seed=1709, fill=0.3, T=400.0, m=64, nfreq=32,
-                                     prec="fp32", method="split2", rtol=1e-7, t_oracle=20.0, batch=32),
+                                     prec="fp32", method="split2", rtol=1e-7, batch=32),
     # the neighbouring-frequency difference (eq. (4diff)) against the plain
     # split, on a 2D cavity whose stationary parts converge: 8 frequencies
     # 0.001 Omega0 apart (the paper's step)
     "2d12_m40_T60_8f_split4d": dict(dim=2, n=12, ndisks=2, seed=1708, T=60.0, m=40, nfreq=8, prec="fp64",
-                                    method="split4d", rtol=1e-11, t_oracle=60.0, batch=8, band=(1.0, 1.007)),
+                                    method="split4d", rtol=1e-11, batch=8, band=(1.0, 1.007)),
     "2d12_m40_T60_8f_split": dict(dim=2, n=12, ndisks=2, seed=1708, T=60.0, m=40, nfreq=8, prec="fp64",
-                                  method="split", rtol=1e-11, t_oracle=60.0, batch=8, band=(1.0, 1.007)),
+                                  method="split", rtol=1e-11, batch=8, band=(1.0, 1.007)),
     # config 1 with the paper's perfectly matched layer (auxiliary field P,
     # quadratic sigma up to 3 over the 6-cell layers)
     "2d64_m30_T200_pml": dict(dim=2, n=64, seed=1708, T=200.0, m=30, nfreq=1, prec="fp64",
-                              method="plain", rtol=1e-11, t_oracle=200.0, pml=True),
+                              method="plain", rtol=1e-11, pml=True),
     # 2D 64^2, 40 disks, FP64, m = 30, T = 200, plain method
     "2d64_m30_T200": dict(dim=2, n=64, seed=1708, T=200.0, m=30, nfreq=1, prec="fp64",
-                          method="plain", rtol=1e-11, t_oracle=200.0),
+                          method="plain", rtol=1e-11),
     # 3D 128^3, 32 frequencies in [0.8, 1.2] Omega0 (the multi-frequency batch)
     "3d128_32f_T400": dict(dim=3, n=128, seed=1710, fill=0.3, T=400.0, m=64, nfreq=32,
-                           prec="fp32", method="plain", rtol=1e-7, t_oracle=4.0, batch=16),
+                           prec="fp32", method="plain", rtol=1e-7, batch=16),
     # uneven batch: 48 instances, sizes U{32..96}^3, 4 frequencies each, concurrent
     "uneven48_4f": dict(kind="uneven", count=48, seed=1711, T=400.0, m=64, nfreq=4, prec="fp32",
                         method="plain", rtol=1e-7, threads=8),
@@ -202,25 +200,75 @@ def barrier_max(dist, value):
     return float(t.item())
 
 
-def oracle_sample(w, sc):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload:
-    one frequency's exact response over [0, t_oracle] by the augmented
-    route (expm_multiply), scaled to the full interval."""
-    from oracle import exact, pml, yee
-    if getattr(sc.grid, "pml", 0):
-        op = pml.PmlOperator(sc.grid, sc.eps_cell)
-    else:
-        op = yee.Operator(sc.grid, sc.eps_cell)
-    A = op.matrix()
-    t_s = min(w["t_oracle"], w["T"])
-    t0 = time.perf_counter()
-    exact.y_plain(A, sc.g, float(sc.omegas[0]), t_s)
-    el = time.perf_counter() - t0
-    per_response = el * (w["T"] / t_s)
-    sample = (f"oracle exact response (augmented system, scipy expm_multiply, FP64) of 1 of "
-              f"{w['nfreq']} frequencies over t in [0, {t_s:g}] of [0, {w['T']:g}] on the full "
-              f"{sc.grid.n} grid; {el:.1f} s scaled x{w['T'] / t_s:g}")
-    return 1.0 / per_response, el, sample
+def config_of(args, w, sc, world=1):
+    """The workload description both arms print."""
+    return {"workload": args.workload, "grid": list(sc.grid.n), "unknowns": sc.grid.nunk,
+            "T": w["T"], "krylov_dim": w["m"], "nfreq": w["nfreq"], "method": w["method"],
+            "projected": "f64", "arnoldi": args.arnoldi, "parallelism": f"replicas{world}",
+            "l2": "working set (Krylov basis) larger than L2; no flush"}
+
+
+class OraclePieces:
+    """The FP64 oracle, as it stands, on the workload's full grid: the exact
+    response y_f(T) by its augmented route (``oracle.exact.y_plain_pieces``,
+    scipy expm_multiply), advanced one sub-interval ("piece") of [0, T] per
+    call, for two seeded frequencies of the workload in turn.
+
+    A response takes ``pieces`` calls, all of the same length and the same
+    work (same matrix, same interval), so responses done = calls / pieces
+    exactly; nothing is extrapolated.  The piece length puts ||dt L||_1 near
+    10 (eta = ||g||_1 keeps the source column of L at unit 1-norm): one
+    Taylor segment of scipy's largest degree and no norm estimation per
+    piece.  One call over all of [0, T] would instead run a norm estimation
+    and then about the same number of operator products per unit time."""
+
+    def __init__(self, w, sc):
+        from oracle import exact, pml, yee
+        self.exact = exact
+        op = pml.PmlOperator(sc.grid, sc.eps_cell) if getattr(sc.grid, "pml", 0) else yee.Operator(sc.grid, sc.eps_cell)
+        t0 = time.perf_counter()
+        self.A = op.matrix()
+        self.setup_s = time.perf_counter() - t0
+        self.g = sc.g
+        self.T = w["T"]
+        nf = len(sc.omegas)
+        rng = np.random.default_rng(1707 + 3)
+        self.picks = sorted(int(i) for i in rng.choice(nf, size=min(2, nf), replace=False))
+        self.omegas = [float(sc.omegas[i]) for i in self.picks]
+        self.eta = float(np.abs(sc.g).sum())
+        L = exact.augmented(self.A, sc.g, self.omegas[0], self.eta)
+        l1 = float(abs(L).sum(axis=0).max())
+        self.pieces = max(1, int(math.ceil(self.T * l1 / 10.0)))
+        self.gens = [None] * len(self.omegas)
+        self.calls = 0
+
+    def step(self):
+        """Advance the next frequency's run by one piece (restarting a run
+        that has reached T); returns the elapsed seconds."""
+        q = self.calls % len(self.gens)
+        self.calls += 1
+        t0 = time.perf_counter()
+        if self.gens[q] is None:
+            self.gens[q] = self.exact.y_plain_pieces(self.A, self.g, self.omegas[q], self.T, self.pieces, self.eta)
+        try:
+            next(self.gens[q])
+        except StopIteration:
+            self.gens[q] = self.exact.y_plain_pieces(self.A, self.g, self.omegas[q], self.T, self.pieces, self.eta)
+            next(self.gens[q])
+        return time.perf_counter() - t0
+
+    def describe(self, calls, secs):
+        return (f"oracle exact response (augmented route, scipy expm_multiply, FP64) on the full "
+                f"{self.A.shape[0]}-unknown grid, frequencies {self.picks} of the workload: "
+                f"{calls} of the {self.pieces} equal pieces of [0, {self.T:g}] a response takes, "
+                f"{secs:.1f} s ({secs / max(calls, 1):.2f} s a piece, {self.pieces * secs / max(calls, 1):.0f} s a "
+                f"response); operator assembly {self.setup_s:.1f} s not counted")
+
+
+def cpu_info():
+    """Host cores (nproc) and the threads the oracle's sparse products use
+    (scipy's CSR product is single-threaded)."""
+    return {"nproc": os.cpu_count(), "threads_used": 1}
 
 
 def run_reference(args, w):
@@ -228,18 +276,23 @@ def run_reference(args, w):
     if rank != 0:
         return
     sc = scenario_for(w)
-    vals = []
-    for _ in range(args.warmup + args.steps):
-        v, el, sample = oracle_sample(w, sc)
-        vals.append(v)
-    v = float(np.mean(vals[args.warmup:])) if args.steps > 0 else float(vals[-1])
+    orc = OraclePieces(w, sc)
+    for _ in range(args.warmup):
+        orc.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.step()
+    el = time.perf_counter() - t0
+    v = (args.steps / orc.pieces) / el if el > 0 else 0.0
+    info = cpu_info()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "responses/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * w["nfreq"] / v, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1000.0 * el / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload},
+            "config": config_of(args, w, sc),
+            "step": "one piece of one frequency's oracle response (1/%d of a response)" % orc.pieces,
             "cpu_baseline": {"kind": "oracle", "value": v, "unit": "responses/s", "cores": 1,
-                             "sample": sample},
+                             "sample": orc.describe(args.steps, el), **info},
             "e2e": {"value": v, "unit": "responses/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -475,34 +528,56 @@ def main():
                 "share_of_step": round(kt[dom]["ms"] / total_ms, 4) if total_ms else None}
 
     # ---- accuracy and the one-frequency-at-a-time comparison (untimed) ------
-    # (a) the batch's first and last responses against FP64 runs of the same
-    #     responses (the FP64 path matches the FP64 oracle to 1e-10 in the
-    #     parity tests); (b) the same frequency solved alone, batch 1.
+    # (a) every response of the batch against the same responses from the
+    #     FP64 path of the same method, and the first and last also against
+    #     the FP64 time-restarted plain method (an independent route; both FP64
+    #     paths match the FP64 oracle to 1e-9 or better in the parity tests);
+    #     (b) the same frequency solved alone, batch 1.
     acc = {}
     pick = sorted({0, w["nfreq"] - 1})
     with torch.cuda.stream(stream):
         full = ctx.response_at_freqs(g, oms, w["T"], rtol=w["rtol"], method=w["method"], plane=sc.plane,
                                      want_full=True)
     stream.synchronize()
+    g64 = torch.tensor(sc.g, dtype=torch.float64, device="cuda")
+
+    def rel_errs(got, ref, idx):
+        fe, pe = {}, {}
+        for q, f in enumerate(idx):
+            a = got["Y"][f].double()
+            b = ref["Y"][q]
+            fe[int(f)] = float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+            pa = got["E_plane"][f].double()
+            pb = ref["E_plane"][q]
+            pe[int(f)] = float(torch.linalg.norm(pa - pb) / torch.linalg.norm(pb))
+        return fe, pe
+
+    if w["method"] == "rstdim":
+        ctx64 = Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=w["m"], max_freqs=w["nfreq"],
+                        batch=2, stream=stream, rst_samples=w.get("rst_samples", 0) * 4)
+        with torch.cuda.stream(stream):
+            ref_all = ctx64.response_at_freqs(g64, oms, w["T"], rtol=1e-11, method="rstdim", plane=sc.plane,
+                                              want_full=True)
+        stream.synchronize()
+        fe, pe = rel_errs(full, ref_all, list(range(w["nfreq"])))
+        acc["rel_l2_field_vs_fp64_same_method"] = fe
+        acc["rel_l2_plane_E_vs_fp64_same_method"] = pe
+        del ref_all
+        ctx64.close()
     ctx64 = Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=w["m"], max_freqs=len(pick),
                     batch=len(pick), stream=stream)
-    g64 = torch.tensor(sc.g, dtype=torch.float64, device="cuda")
     with torch.cuda.stream(stream):
         ref = ctx64.response_at_freqs(g64, oms[pick], w["T"], rtol=1e-11, method="plain", plane=sc.plane,
                                       want_full=True)
     stream.synchronize()
-    errs, perrs = [], []
-    for q, f in enumerate(pick):
-        a = full["Y"][f].double().cpu().numpy()
-        b = ref["Y"][q].cpu().numpy()
-        errs.append(float(np.linalg.norm(a - b) / np.linalg.norm(b)))
-        pa = full["E_plane"][f].double().cpu().numpy()
-        pb = ref["E_plane"][q].cpu().numpy()
-        perrs.append(float(np.linalg.norm(pa - pb) / np.linalg.norm(pb)))
-    acc["rel_l2_field_vs_fp64"] = dict(zip([int(f) for f in pick], errs))
-    acc["rel_l2_plane_E_vs_fp64"] = dict(zip([int(f) for f in pick], perrs))
-    acc["max_rel_l2"] = max(errs)
-    acc["max_rel_l2_plane_E"] = max(perrs)
+    fe, pe = rel_errs(full, ref, pick)
+    acc["rel_l2_field_vs_fp64"] = fe
+    acc["rel_l2_plane_E_vs_fp64"] = pe
+    allf = list(fe.values()) + list(acc.get("rel_l2_field_vs_fp64_same_method", {}).values())
+    allp = list(pe.values()) + list(acc.get("rel_l2_plane_E_vs_fp64_same_method", {}).values())
+    acc["max_rel_l2"] = max(allf)
+    acc["max_rel_l2_plane_E"] = max(allp)
+    acc["frequencies_checked"] = w["nfreq"] if w["method"] == "rstdim" else len(pick)
     ctx64.close()
     single = None
     if w.get("batch", 1) > 1 or w["method"] == "rstdim":
@@ -521,20 +596,19 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, el, sample = oracle_sample(w, sc)
-        cpu = {"value": v, "unit": "responses/s", "cores": 1, "kind": "oracle", "sample": sample}
+        orc = OraclePieces(w, sc)
+        nc = 3
+        el = sum(orc.step() for _ in range(nc))
+        cpu = {"value": (nc / orc.pieces) / el, "unit": "responses/s", "cores": 1, "kind": "oracle",
+               "sample": orc.describe(nc, el), **cpu_info()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "responses/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if w["prec"] == "fp32" else "f64", "data": "synthetic",
-                "config": {"workload": args.workload, "grid": list(sc.grid.n), "unknowns": sc.grid.nunk,
-                           "T": w["T"], "krylov_dim": w["m"], "nfreq": w["nfreq"], "method": w["method"],
-                           "projected": "f64", "arnoldi": args.arnoldi,
-                           "arnoldi_ran": "single sweep" if kt["sweep"]["launches"] else "two-pass",
-                           "parallelism": f"replicas{world}",
-                           "l2": "working set (Krylov basis) larger than L2; no flush"},
+                "config": config_of(args, w, sc, world),
+                "arnoldi_ran": "single sweep" if kt["sweep"]["launches"] else "two-pass",
                 "roofline": roofline,
                 "arnoldi_hbm_gbs": round(ab_gbs, 1),
                 "krylov_steps_per_s": round(krylov_steps * world / (dev_ms / 1000.0), 1),

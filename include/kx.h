@@ -132,6 +132,21 @@ typedef struct {
 kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell,
                              void* cuda_stream, kx_ctx** out);
 
+/* Create a context from a material id per cell (the layout Sect. 4.1's
+ * media suggest: a few materials, each cell in one of them).
+ *   d_mat_id : DEVICE array of n[0]*n[1](*n[2]) material ids (uint8, x
+ *              fastest), caller-owned; read during this call only.
+ *   eps_table: HOST array of n_mat relative permittivities (> 0, finite);
+ *              cell c gets eps_table[d_mat_id[c]].
+ *   n_mat    : 1 .. KX_MAX_MATERIALS.
+ * Everything else as for krylov_expm_create (the per-cell permittivity is
+ * expanded on the device and kept, so kx_set_permittivity and the adjoint's
+ * per-cell gradient work as for a context made from eps_cell).
+ * Errors: those of krylov_expm_create, and KX_EINVAL when an id is >= n_mat. */
+#define KX_MAX_MATERIALS 64
+kx_status krylov_expm_create_mat(const kx_desc* desc, const uint8_t* d_mat_id, const double* eps_table,
+                                 int n_mat, void* cuda_stream, kx_ctx** out);
+
 /* Release a context and its workspace.  NULL is accepted. */
 kx_status krylov_expm_destroy(kx_ctx* ctx);
 
@@ -350,17 +365,19 @@ const char* kx_last_error(const kx_ctx* ctx);
  * in this library's kernels is bounded (the single-sweep Arnoldi waits on
  * mbarriers for its basis copies); when a wait runs out the kernel records
  * KX_ETIMEOUT, returns normally and the context stays usable.  This call
- * runs that wait, `rounds` try_wait rounds (>= 1), on an mbarrier that
+ * runs that wait, `rounds` try_wait rounds (1 .. KX_WAIT_SELFTEST_MAX_ROUNDS,
+ * the limit of one wait in the library's own kernels), on an mbarrier that
  * nothing completes and no copy targets.  Synchronises the stream.
- * Returns KX_ETIMEOUT (the expected outcome), KX_EINVAL (rounds == 0) or
- * KX_ECUDA. */
+ * Returns KX_ETIMEOUT (the expected outcome), KX_EINVAL (rounds out of
+ * range) or KX_ECUDA. */
+#define KX_WAIT_SELFTEST_MAX_ROUNDS (4194304u)
 kx_status kx_wait_selftest(kx_ctx* ctx, unsigned rounds);
 
 /* Allocation-free Arnoldi (the paper has no counterpart: this is a
  * deployment convenience).  Some callers cannot allocate device memory at
- * all -- code running inside another runtime's memory pool or a captured
- * graph, plug-ins handed a fixed arena, services that forbid cudaMalloc and
- * cudaFree after start-up -- and so cannot create a context.  This call needs
+ * all -- code running inside another runtime's memory pool, plug-ins handed
+ * a fixed arena, services that forbid cudaMalloc and cudaFree after
+ * start-up -- and so cannot create a context.  This call needs
  * no context and performs no device allocation: the caller passes every
  * input and output, the basis array d_V doubles as the Krylov workspace, and
  * the remaining scratch (block partial sums, column scales, the step state
@@ -377,7 +394,8 @@ kx_status kx_wait_selftest(kx_ctx* ctx, unsigned rounds);
  *               with n * sizeof(scalar) a multiple of 16 (KX_EINVAL
  *               otherwise); returned orthonormal as by arnoldi().
  *   d_H       : device (m+1) x m FP64 Hessenberg matrix (column-major).
- *   beta, m_done: host outputs as for arnoldi().
+ *   beta, m_done: host outputs as for arnoldi(); a zero or non-finite v0
+ *               is refused (KX_ENONFINITE) before any Arnoldi step runs.
  * Results match arnoldi() on a context with the same descriptor and
  * arnoldi_form KX_ARN_DEFAULT or KX_ARN_TWOPASS (this entry runs the
  * two-pass form whatever the descriptor's arnoldi_form).  The call

@@ -29,12 +29,11 @@ def augmented(A, g, omega, eta=1.0):
     return sp.vstack([top, bot]).tocsr()
 
 
-def y_plain(A, g, omega, T, eta=None, pieces=1):
-    """y(T) from exp(T L) [0; 0; eta], L from :func:`augmented`.
-
-    ``pieces`` splits [0, T] into equal sub-intervals (the exponential is
-    exact on each one; this only bounds the work of one expm_multiply call).
-    """
+def y_plain_pieces(A, g, omega, T, pieces, eta=None):
+    """The augmented route of :func:`y_plain` one sub-interval at a time:
+    yields (k, y(k T / pieces)) for k = 1 .. pieces, where y(t) is the first
+    n entries of exp(t L) [0; 0; eta] and each step applies exp((T / pieces) L)
+    to the previous state (the exponential is exact on every sub-interval)."""
     n = A.shape[0]
     if eta is None:
         eta = max(float(np.linalg.norm(g)), 1e-300)
@@ -42,9 +41,21 @@ def y_plain(A, g, omega, T, eta=None, pieces=1):
     x = np.zeros(n + 2)
     x[n + 1] = eta
     dt = T / pieces
-    for _ in range(pieces):
+    for k in range(1, pieces + 1):
         x = spla.expm_multiply(dt * L, x)
-    return x[:n]
+        yield k, x[:n]
+
+
+def y_plain(A, g, omega, T, eta=None, pieces=1):
+    """y(T) from exp(T L) [0; 0; eta], L from :func:`augmented`.
+
+    ``pieces`` splits [0, T] into equal sub-intervals (the exponential is
+    exact on each one; this only bounds the work of one expm_multiply call).
+    """
+    y = None
+    for _, y in y_plain_pieces(A, g, omega, T, pieces, eta):
+        pass
+    return y
 
 
 def z_stat(A, g, omega):

@@ -24,7 +24,7 @@ METHODS = {"plain": KX_PLAIN, "split": KX_SPLIT, "rstdim": KX_RSTDIM, "split2": 
 STATUS_NAMES = {0: "KX_OK", 1: "KX_EINVAL", 2: "KX_ENOMEM", 3: "KX_ECUDA",
                 4: "KX_ENONFINITE", 5: "KX_ENOCONV", 6: "KX_ETIMEOUT"}
 
-EXPORTS = ["krylov_expm_create", "krylov_expm_destroy", "kx_num_unknowns", "apply_A",
+EXPORTS = ["krylov_expm_create", "krylov_expm_create_mat", "krylov_expm_destroy", "kx_num_unknowns", "apply_A",
            "arnoldi", "expm_phi_project", "stationary_solve", "expm_action",
            "response_at_freqs", "kx_get_stats", "kx_reset_stats", "kx_set_timing",
            "kx_kernel_times", "kx_last_error", "kx_arnoldi_noalloc", "kx_noalloc_last_error",
@@ -74,6 +74,7 @@ def load_library(path: Optional[str] = None):
     lib = ctypes.CDLL(p)
     vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
     lib.krylov_expm_create.argtypes = [ctypes.POINTER(Desc), dp, vp, ctypes.POINTER(vp)]
+    lib.krylov_expm_create_mat.argtypes = [ctypes.POINTER(Desc), vp, dp, ctypes.c_int, vp, ctypes.POINTER(vp)]
     lib.krylov_expm_destroy.argtypes = [vp]
     lib.kx_num_unknowns.argtypes = [vp]
     lib.kx_num_unknowns.restype = ctypes.c_int64
@@ -132,11 +133,14 @@ class Context:
     ``arnoldi``: "default" (single sweep for restart in dimension on grids of
     3e6 unknowns or more, two passes elsewhere), "twopass" or "sweep" (also
     for ``arnoldi()``).
+    ``mat_id`` / ``eps_table``: instead of ``eps_cell`` (pass None), a CUDA
+    uint8 tensor of material ids per cell and the materials' permittivities
+    (``krylov_expm_create_mat``).
     """
 
     def __init__(self, grid, eps_cell, precision: str = "fp32", krylov_dim: int = 64,
                  max_freqs: int = 1, batch: int = 1, stream=None, max_checkpoints: int = 0,
-                 rst_samples: int = 0, arnoldi: str = "default"):
+                 rst_samples: int = 0, arnoldi: str = "default", mat_id=None, eps_table=None):
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -164,10 +168,18 @@ class Context:
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         own = isinstance(stream, str) and stream == "own"
         self.stream = None if own else (stream if stream is not None else torch.cuda.current_stream())
-        eps = np.ascontiguousarray(np.asarray(eps_cell, np.float64).reshape(-1))
         h = ctypes.c_void_p()
         sarg = ctypes.c_void_p(-1) if own else ctypes.c_void_p(self.stream.cuda_stream)
-        st = self.lib.krylov_expm_create(ctypes.byref(d), _dptr(eps), sarg, ctypes.byref(h))
+        if eps_cell is None:
+            if not (isinstance(mat_id, torch.Tensor) and mat_id.is_cuda and mat_id.dtype == torch.uint8):
+                raise TypeError("mat_id must be a CUDA uint8 tensor")
+            mid = mat_id.contiguous()
+            tab = np.ascontiguousarray(np.asarray(eps_table, np.float64).reshape(-1))
+            st = self.lib.krylov_expm_create_mat(ctypes.byref(d), ctypes.c_void_p(mid.data_ptr()), _dptr(tab),
+                                                 len(tab), sarg, ctypes.byref(h))
+        else:
+            eps = np.ascontiguousarray(np.asarray(eps_cell, np.float64).reshape(-1))
+            st = self.lib.krylov_expm_create(ctypes.byref(d), _dptr(eps), sarg, ctypes.byref(h))
         if st != KX_OK:
             raise KxError(st, self.lib.kx_last_error(None).decode())
         self.h = h

@@ -320,12 +320,9 @@ kx_status launch_adj_substep(kx_ctx* c, double tau, double omega, double tk, con
     return KX_EINVAL;
   }
   const int m = c->m;
-  static std::atomic<int> attr{0};
-  if (!attr) {
-    cudaFuncSetAttribute(k_adj_coeffs, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)expm_smem_bytes(MMAX + 2));
-    attr = 1;
-  }
+  static SmemOptIn attr{};
+  const kx_status so = smem_opt_in(c, attr, (const void*)k_adj_coeffs, expm_smem_bytes(MMAX + 2));
+  if (so != KX_OK) return so;
   int* status = reinterpret_cast<int*>(c->d_small + 64);
   time_begin(c);
   k_adj_coeffs<<<2, 256, expm_smem_bytes(m), c->stream>>>(

@@ -154,6 +154,15 @@ kx_status capture_substep(kx_ctx* c, int slot0, int ns, const void* g_aug, Subst
   return KX_OK;
 }
 
+// Convergence is decided on the device: the step control retires a slot once
+// it reaches its final time, and every kernel of a later sub-step returns at
+// once for a retired slot (or one whose status records a failure).  The host
+// therefore queues several sub-steps between two reads of the slot states --
+// as many as the slowest slot is predicted to need, from its mean accepted
+// sub-step so far, capped at SUBSTEP_BATCH -- instead of synchronising after
+// every sub-step; queued sub-steps past the end cost only empty launches.
+constexpr int SUBSTEP_BATCH = 8;
+
 kx_status time_loop(kx_ctx* c, int slot0, int ns, const void* g_aug, double* err_est) {
   KX_TRY(launch_norm_init(c, slot0, ns));
   const int max_sub = 20000;
@@ -163,19 +172,25 @@ kx_status time_loop(kx_ctx* c, int slot0, int ns, const void* g_aug, double* err
   // per-kernel timing is on
   bool use_graph = c->stream != nullptr && !c->timing;
   SubstepGraph graph;
-  for (int it = 0; it < max_sub && !all; ++it) {
-    if (use_graph && it >= 1 && !graph.exec && capture_substep(c, slot0, ns, g_aug, &graph) != KX_OK)
-      use_graph = false;
-    if (use_graph && graph.exec) {
-      KX_CUDA(c, cudaGraphLaunch(graph.exec, c->stream), "sub-step graph launch");
-      c->stats.kernel_launches += graph.launches;
-      c->stats.arnoldi_steps += (int64_t)c->m * ns;
-      c->stats.matvecs += (int64_t)c->m * ns;
-    } else {
-      KX_TRY(substep_launches(c, slot0, ns, g_aug));
+  int queued = 0, batch = 1;
+  while (queued < max_sub && !all) {
+    for (int b = 0; b < batch && queued < max_sub; ++b, ++queued) {
+      if (use_graph && queued >= 1 && !graph.exec && capture_substep(c, slot0, ns, g_aug, &graph) != KX_OK)
+        use_graph = false;
+      if (use_graph && graph.exec) {
+        KX_CUDA(c, cudaGraphLaunch(graph.exec, c->stream), "sub-step graph launch");
+        c->stats.kernel_launches += graph.launches;
+      } else {
+        const kx_stats before = c->stats;
+        KX_TRY(substep_launches(c, slot0, ns, g_aug));
+        // Arnoldi work is counted from the accepted sub-steps below
+        c->stats.arnoldi_steps = before.arnoldi_steps;
+        c->stats.matvecs = before.matvecs;
+      }
     }
     KX_TRY(read_states(c, slot0, ns));
     all = true;
+    double need = 1.0;
     for (int q = 0; q < ns; ++q) {
       const SlotState& st = c->h_state[slot0 + q];
       if (st.status)
@@ -183,13 +198,19 @@ kx_status time_loop(kx_ctx* c, int slot0, int ns, const void* g_aug, double* err
                     st.status == KX_ENOCONV ? "time sub-step control: no step length met the tolerance"
                                             : "non-finite value in the Krylov process");
       all = all && st.retired;
+      if (!st.retired && st.substeps > 0 && st.t_now > 0.0)
+        need = std::max(need, std::ceil((st.T - st.t_now) * st.substeps / st.t_now));
     }
+    batch = (int)std::min<double>(SUBSTEP_BATCH, need);
   }
   if (!all) return fail(c, KX_ENOCONV, "time stepping: sub-step cap reached");
   for (int q = 0; q < ns; ++q) {
     const SlotState& st = c->h_state[slot0 + q];
     c->stats.substeps += st.substeps;
     c->stats.expm_evals += st.expm_evals;
+    // one m-step Arnoldi process per accepted sub-step
+    c->stats.arnoldi_steps += (int64_t)c->m * st.substeps;
+    c->stats.matvecs += (int64_t)c->m * st.substeps;
     if (err_est) err_est[q] = st.err_acc;
   }
   return KX_OK;
@@ -381,9 +402,16 @@ kx_status split2_wave(kx_ctx* c, const void* d_g, const double* omegas, int f0, 
 // ===========================================================================
 extern "C" {
 
-kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* cuda_stream,
-                             kx_ctx** out) {
-  if (!desc || !eps_cell || !out) return fail(nullptr, KX_EINVAL, "NULL argument");
+}  // extern "C"
+
+namespace {
+
+// Context creation.  The permittivity comes either from a host array per
+// cell (eps_cell) or from a device array of material ids per cell and a host
+// table of their permittivities (d_mat_id, eps_table, n_mat).
+kx_status create_impl(const kx_desc* desc, const double* eps_cell, const uint8_t* d_mat_id,
+                      const double* eps_table, int n_mat, void* cuda_stream, kx_ctx** out) {
+  if (!desc || !out || (!eps_cell && !(d_mat_id && eps_table))) return fail(nullptr, KX_EINVAL, "NULL argument");
   *out = nullptr;
   const kx_desc& d = *desc;
   if (d.dim != 2 && d.dim != 3) return fail(nullptr, KX_EINVAL, "dim must be 2 or 3");
@@ -410,9 +438,16 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
     return fail(nullptr, KX_EINVAL, "arnoldi_form must be KX_ARN_DEFAULT, KX_ARN_TWOPASS or KX_ARN_SWEEP");
   const int nz = d.dim == 3 ? d.n[2] : 1;
   const int64_t ncell = (int64_t)d.n[0] * d.n[1] * nz;
-  for (int64_t i = 0; i < ncell; ++i)
-    if (!(eps_cell[i] > 0.0) || !std::isfinite(eps_cell[i]))
-      return fail(nullptr, KX_ENONFINITE, "eps_cell must be finite and > 0");
+  if (eps_cell) {
+    for (int64_t i = 0; i < ncell; ++i)
+      if (!(eps_cell[i] > 0.0) || !std::isfinite(eps_cell[i]))
+        return fail(nullptr, KX_ENONFINITE, "eps_cell must be finite and > 0");
+  } else {
+    if (n_mat < 1 || n_mat > KX_MAX_MATERIALS) return fail(nullptr, KX_EINVAL, "n_mat must be 1 .. 64");
+    for (int i = 0; i < n_mat; ++i)
+      if (!(eps_table[i] > 0.0) || !std::isfinite(eps_table[i]))
+        return fail(nullptr, KX_ENONFINITE, "eps_table entries must be finite and > 0");
+  }
 
   kx_ctx* c = new (std::nothrow) kx_ctx();
   if (!c) return fail(nullptr, KX_ENOMEM, "host allocation failed");
@@ -581,13 +616,21 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_V, 0, bytes_V, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_aug, 0, (size_t)B * (m + 1) * 2 * sizeof(double), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_H, 0, (size_t)B * (m + 1) * m * sizeof(double), c->stream);
-  if (e == cudaSuccess)
+  int* d_bad = reinterpret_cast<int*>(c->d_small + KX_MAX_MATERIALS);
+  if (e == cudaSuccess && eps_cell) {
     e = cudaMemcpyAsync(c->d_eps_cell, eps_cell, (size_t)ncell * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  } else if (e == cudaSuccess) {
+    // the table and the id check flag go through the small scratch buffer
+    std::memcpy(c->h_small, eps_table, sizeof(double) * n_mat);
+    e = cudaMemcpyAsync(c->d_small, c->h_small, sizeof(double) * n_mat, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream);
+  }
   if (e != cudaSuccess) {
     krylov_expm_destroy(c);
     return fail(nullptr, KX_ECUDA, std::string("initialisation failed: ") + cudaGetErrorString(e));
   }
-  kx_status st = launch_setup_material(c);
+  kx_status st = eps_cell ? KX_OK : launch_expand_materials(c, d_mat_id, c->d_small, n_mat, d_bad);
+  if (st == KX_OK) st = launch_setup_material(c);
   if (st == KX_OK) {
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) st = KX_ECUDA, snprintf(c->err, sizeof(c->err), "%s", cudaGetErrorString(e));
@@ -597,9 +640,34 @@ kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* 
     krylov_expm_destroy(c);
     return fail(nullptr, st, "material set-up failed: " + msg);
   }
+  if (!eps_cell) {
+    int bad = 0;
+    e = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess || bad) {
+      krylov_expm_destroy(c);
+      return fail(nullptr, e != cudaSuccess ? KX_ECUDA : KX_EINVAL,
+                  e != cudaSuccess ? std::string("material check read-back: ") + cudaGetErrorString(e)
+                                   : std::string("a material id is >= n_mat"));
+    }
+  }
   std::memset(&c->stats, 0, sizeof(c->stats));
   *out = c;
   return KX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kx_status krylov_expm_create(const kx_desc* desc, const double* eps_cell, void* cuda_stream, kx_ctx** out) {
+  if (!eps_cell) return fail(nullptr, KX_EINVAL, "NULL argument");
+  return create_impl(desc, eps_cell, nullptr, nullptr, 0, cuda_stream, out);
+}
+
+kx_status krylov_expm_create_mat(const kx_desc* desc, const uint8_t* d_mat_id, const double* eps_table, int n_mat,
+                                 void* cuda_stream, kx_ctx** out) {
+  if (!d_mat_id || !eps_table) return fail(nullptr, KX_EINVAL, "NULL argument");
+  return create_impl(desc, nullptr, d_mat_id, eps_table, n_mat, cuda_stream, out);
 }
 
 kx_status krylov_expm_destroy(kx_ctx* c) {
@@ -1306,7 +1374,8 @@ extern "C" {
 
 kx_status kx_wait_selftest(kx_ctx* c, unsigned rounds) {
   if (!c) return KX_EINVAL;
-  if (rounds == 0) return fail(c, KX_EINVAL, "rounds must be >= 1");
+  if (rounds == 0 || rounds > KX_WAIT_SELFTEST_MAX_ROUNDS)
+    return fail(c, KX_EINVAL, "rounds must be 1 .. KX_WAIT_SELFTEST_MAX_ROUNDS (4194304)");
   int* d_status = reinterpret_cast<int*>(c->d_small + 200);
   KX_CUDA(c, cudaMemsetAsync(d_status, 0xff, sizeof(int), c->stream), "status reset");
   KX_TRY(launch_wait_selftest(c, rounds, d_status));
@@ -1356,6 +1425,31 @@ int persistent_grid(kx_ctx* c, const void* kernel, int64_t rounds, size_t smem) 
   }
   const int64_t cap = std::min<int64_t>((int64_t)c->nsm * occ, c->ps);
   return (int)std::max<int64_t>(1, std::min<int64_t>(rounds, cap));
+}
+
+kx_status smem_opt_in(kx_ctx* c, SmemOptIn& rec, const void* kernel, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(c->err, sizeof(c->err), "cudaGetDevice: %s", cudaGetErrorString(e));
+    return KX_ECUDA;
+  }
+  if (dev < 0 || dev >= SMEM_MAX_DEVICES) {
+    snprintf(c->err, sizeof(c->err), "device index %d beyond %d", dev, SMEM_MAX_DEVICES);
+    return KX_EINVAL;
+  }
+  if (__atomic_load_n(&rec.done[dev], __ATOMIC_ACQUIRE)) return KX_OK;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(c->err, sizeof(c->err), "setting %zu bytes of dynamic shared memory: %s", bytes,
+             cudaGetErrorString(e));
+    return KX_ECUDA;
+  }
+  // stored after the attribute is in place: a thread that sees the flag may launch
+  __atomic_store_n(&rec.done[dev], 1, __ATOMIC_RELEASE);
+  return KX_OK;
 }
 
 }  // namespace kx

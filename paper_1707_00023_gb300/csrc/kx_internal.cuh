@@ -237,6 +237,8 @@ namespace kx {
 
 // stencil.cu  (slot0, ns: the consecutive slots [slot0, slot0 + ns) advance together)
 kx_status launch_setup_material(kx_ctx* c);
+// d_eps_cell[i] = d_table[d_id[i]]; *d_bad = 1 if an id is >= n_mat
+kx_status launch_expand_materials(kx_ctx* c, const uint8_t* d_id, const double* d_table, int n_mat, int* d_bad);
 kx_status launch_apply(kx_ctx* c, const void* v, void* w, int transpose);
 kx_status launch_pass_a(kx_ctx* c, int slot0, int ns, int j, const void* g_aug);
 // pass A with the transposed operator A^T
@@ -300,6 +302,17 @@ size_t expm_smem_bytes(int msz);
 // Persistent grid for a kernel: resident blocks (occupancy) x SMs, capped
 // by the work and by the partial-sum stride.
 int persistent_grid(kx_ctx* c, const void* kernel, int64_t items_per_block_round, size_t smem);
+
+// Opt-in of a kernel to more than 48 KB of dynamic shared memory.  The
+// attribute belongs to the device that is current when it is set, so the
+// record of which devices have it is kept per device; a set that fails is
+// not recorded, and the caller gets KX_ECUDA (with the reason in c->err)
+// instead of a launch that would fail later.
+constexpr int SMEM_MAX_DEVICES = 64;
+struct SmemOptIn {
+  int done[SMEM_MAX_DEVICES];   // accessed atomically (1: set on that device)
+};
+kx_status smem_opt_in(kx_ctx* c, SmemOptIn& rec, const void* kernel, size_t bytes);
 
 // Programmatic dependent launch.  A kernel of the Arnoldi chain may be
 // launched while its predecessor in the stream is still running; it waits

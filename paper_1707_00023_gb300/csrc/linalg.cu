@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(NTHREADS) k_restart(SlotSet<T> ss, int64_t n, 
   using V4 = typename Vec<T>::t;
   constexpr int W = Vec<T>::w;
   const Slot<T> s = slot_at(ss, blockIdx.y);
-  if (s.st->retired) return;
+  // retired, or (combination) a failed sub-step: nothing to combine
+  if (s.st->retired || (mode == 1 && s.st->status)) return;
   __shared__ T coef[MMAX];
   __shared__ float coef_lo[MMAX];
   int m = 0;
@@ -431,14 +432,10 @@ __global__ void __launch_bounds__(NTHREADS) k_zupdate(const T* __restrict__ V, i
 
 kx_status launch_zupdate(kx_ctx* c, int slot, int nfreq, void* zre, void* zim, int m) {
   const size_t sm = (size_t)2 * nfreq * MMAX * c->esize;
-  static std::atomic<int> attr_done{0};
-  if (!attr_done) {
-    cudaFuncSetAttribute(k_zupdate<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(2 * MAXF * MMAX * sizeof(double)));
-    cudaFuncSetAttribute(k_zupdate<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(2 * MAXF * MMAX * sizeof(float)));
-    attr_done = 1;
-  }
+  static SmemOptIn attr_d{}, attr_f{};
+  kx_status so = smem_opt_in(c, attr_d, (const void*)k_zupdate<double>, 2 * MAXF * MMAX * sizeof(double));
+  if (so == KX_OK) so = smem_opt_in(c, attr_f, (const void*)k_zupdate<float>, 2 * MAXF * MMAX * sizeof(float));
+  if (so != KX_OK) return so;
   // bytes: read m basis columns, read and write 2 nfreq stationary vectors
   time_begin(c);
   struct End { kx_ctx* c; int m, nf; ~End() { time_end(c, KX_K_ZUPDATE, (m + 4.0 * nf) * c->n * c->esize); } } end{c, m, nfreq};

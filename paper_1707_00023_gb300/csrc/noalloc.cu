@@ -2,8 +2,8 @@
 // include/kx.h).
 //
 // Some callers cannot allocate device memory: code running inside another
-// runtime's memory pool or graph, plug-ins handed a fixed arena, or hosts
-// that forbid cudaMalloc/cudaFree after start-up.  This entry point needs no
+// runtime's memory pool, plug-ins handed a fixed arena, or hosts that forbid
+// cudaMalloc/cudaFree after start-up.  This entry point needs no
 // context and allocates nothing.  The caller passes every input and output
 // (the permittivity per cell, the start vector, the basis and Hessenberg
 // arrays); the basis array doubles as the Krylov workspace, and the remaining
@@ -15,7 +15,10 @@
 // work overlaps on the GPU (different streams, or host threads without
 // ordering) race on it.  Every GPU that loads the library holds the array
 // until the process exits.
+#include <atomic>
 #include <cstring>
+
+#include <cmath>
 
 #include "kx_internal.cuh"
 
@@ -39,9 +42,10 @@ constexpr size_t SCRATCH_USED = COUNTER_OFF + 8 * sizeof(unsigned);
 static_assert(SCRATCH_USED <= KX_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the static array");
 
 // Device address of the array, per device (host code cannot use the symbol
-// itself: in host code it names a host-side stand-in).
+// itself: in host code it names a host-side stand-in).  Host threads may
+// fill an entry at the same time; they store the same address.
 constexpr int MAX_DEVICES = 64;
-void* g_scratch_addr[MAX_DEVICES] = {nullptr};
+std::atomic<void*> g_scratch_addr[MAX_DEVICES];
 
 thread_local char g_err[512] = {0};
 
@@ -61,13 +65,13 @@ kx_status scratch_for_current_device(void** out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_err(e, "cudaGetDevice");
   if (dev < 0 || dev >= MAX_DEVICES) return err(KX_EINVAL, "device index beyond 64");
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
+  void* p = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!p) {
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_err(e, "cudaGetSymbolAddress of the scratch array");
-    g_scratch_addr[dev] = p;
+    g_scratch_addr[dev].store(p, std::memory_order_release);
   }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return KX_OK;
 }
 
@@ -163,18 +167,22 @@ extern "C" kx_status kx_arnoldi_noalloc(const kx_desc* desc, const double* d_eps
   if (e != cudaSuccess) return cuda_err(e, "scratch initialisation");
 
   if ((st = launch_norm_init(&c, 0, 1)) != KX_OK) return err(st, c.err);
+  // refuse a zero or non-finite start vector before any step (as arnoldi() does)
+  SlotState hs;
+  e = cudaMemcpyAsync(&hs, c.d_state, sizeof(SlotState), cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return cuda_err(e, "start-vector norm read-back");
+  if (!(hs.beta > 0.0) || !std::isfinite(hs.beta)) return err(KX_ENONFINITE, "v0 is zero or non-finite");
   for (int j = 0; j < m; ++j) {
     if ((st = launch_pass_a_cells(&c, 0, j, d_eps_cell)) != KX_OK) return err(st, c.err);
     if ((st = launch_pass_b(&c, 0, 1, j, j == m - 1)) != KX_OK) return err(st, c.err);
   }
   // normalise the basis in place (the stored columns carry their scales)
   if ((st = launch_basis_export(&c, 0, d_V, m)) != KX_OK) return err(st, c.err);
-  SlotState hs;
   e = cudaMemcpyAsync(&hs, c.d_state, sizeof(SlotState), cudaMemcpyDeviceToHost, c.stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
   if (e != cudaSuccess) return cuda_err(e, "result read-back");
   if (hs.status) return err((kx_status)hs.status, "non-finite value in the Arnoldi process");
-  if (!(hs.beta > 0.0)) return err(KX_ENONFINITE, "v0 is zero or non-finite");
   *beta = hs.beta;
   *m_done = hs.m_done;
   return KX_OK;

@@ -79,7 +79,11 @@ __global__ void __launch_bounds__(256) k_substep(SlotSet<float> ss, int ldh, int
     double* X = cta_expm(buf, m, red, lv, &piv);
     ++evals;
     if (!X) {
-      if (threadIdx.x == 0) st->status = KX_ENONFINITE;
+      // a failed slot stops: the later kernels of queued sub-steps skip it
+      if (threadIdx.x == 0) {
+        st->status = KX_ENONFINITE;
+        st->done = 1;
+      }
       return;
     }
     // tabulate u(t_k)
@@ -119,6 +123,7 @@ __global__ void __launch_bounds__(256) k_substep(SlotSet<float> ss, int ldh, int
     st->expm_evals += evals;
     if (s_kacc == 0) {
       st->status = KX_ENOCONV;
+      st->done = 1;
       return;
     }
     const double tau = s_tau;
@@ -139,11 +144,9 @@ __global__ void __launch_bounds__(256) k_substep(SlotSet<float> ss, int ldh, int
 kx_status launch_substep_control(kx_ctx* c, int slot, int ns) {
   const int m = c->m;
   const size_t sm = expm_smem_bytes(m);
-  static std::atomic<int> attr_done{0};
-  if (!attr_done) {
-    cudaFuncSetAttribute(k_substep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)expm_smem_bytes(MMAX + 2));
-    attr_done = 1;
-  }
+  static SmemOptIn attr{};
+  const kx_status so = smem_opt_in(c, attr, (const void*)k_substep, expm_smem_bytes(MMAX + 2));
+  if (so != KX_OK) return so;
   time_begin(c);
   k_substep<<<ns, 256, sm, c->stream>>>(make_slotset<float>(c, slot), m + 1, 32);
   time_end(c, KX_K_PROJ, 0.0);
@@ -193,12 +196,9 @@ __global__ void __launch_bounds__(256) k_expm_project(const double* H, int ldh, 
 kx_status launch_expm_project(kx_ctx* c, const double* dH, int ldh, int m, double beta, double tau,
                               const double* d_om, int nfreq, double* d_u) {
   const int n = nfreq > 0 ? m + 2 : m;
-  static std::atomic<int> attr_done{0};
-  if (!attr_done) {
-    cudaFuncSetAttribute(k_expm_project, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)expm_smem_bytes(MMAX + 2));
-    attr_done = 1;
-  }
+  static SmemOptIn attr{};
+  const kx_status so = smem_opt_in(c, attr, (const void*)k_expm_project, expm_smem_bytes(MMAX + 2));
+  if (so != KX_OK) return so;
   int* status = reinterpret_cast<int*>(c->d_small + 64);
   time_begin(c);
   k_expm_project<<<nfreq > 0 ? nfreq : 1, 256, expm_smem_bytes(n), c->stream>>>(
@@ -310,12 +310,10 @@ kx_status launch_shifted_solve(kx_ctx* c, int slot, int nfreq, int m) {
   Slot<double> s = make_slot<double>(c, slot);
   int* status = reinterpret_cast<int*>(c->d_small + 64);
   const size_t sm = (size_t)m * m * sizeof(cplx);
-  static std::atomic<int> attr_done{0};
-  if (!attr_done) {
-    cudaFuncSetAttribute(k_shifted<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(MMAX * MMAX * sizeof(cplx)));
-    cudaFuncSetAttribute(k_shifted<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(MMAX * MMAX * sizeof(cplx)));
-    attr_done = 1;
-  }
+  static SmemOptIn attr_f{}, attr_d{};
+  kx_status so = smem_opt_in(c, attr_f, (const void*)k_shifted<float>, MMAX * MMAX * sizeof(cplx));
+  if (so == KX_OK) so = smem_opt_in(c, attr_d, (const void*)k_shifted<double>, MMAX * MMAX * sizeof(cplx));
+  if (so != KX_OK) return so;
   time_begin(c);
   struct End { kx_ctx* c; ~End() { time_end(c, KX_K_PROJ, 0.0); } } end{c};
   if (c->d.precision == KX_FP64)

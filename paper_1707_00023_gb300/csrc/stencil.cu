@@ -48,6 +48,29 @@ __global__ void k_setup_inv_eps(Geo g, const double* __restrict__ eps, T* __rest
   }
 }
 
+// Per-cell permittivity from a material id per cell and a table of the
+// materials' permittivities.  An id outside the table flags *bad and leaves
+// that cell at 1 (the caller then refuses the context).
+__global__ void k_expand_materials(int64_t ncell, const uint8_t* __restrict__ id, const double* __restrict__ table,
+                                   int n_mat, double* __restrict__ eps, int* bad) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ncell; t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = id[t];
+    if (k < n_mat) {
+      eps[t] = table[k];
+    } else {
+      eps[t] = 1.0;
+      *bad = 1;
+    }
+  }
+}
+
+kx_status launch_expand_materials(kx_ctx* c, const uint8_t* d_id, const double* d_table, int n_mat, int* d_bad) {
+  const int64_t blocks = std::min<int64_t>((c->geo.ncell + 255) / 256, (int64_t)c->nsm * 16);
+  k_expand_materials<<<(int)blocks, 256, 0, c->stream>>>(c->geo.ncell, d_id, d_table, n_mat, c->d_eps_cell, d_bad);
+  KX_CHECK_LAUNCH(c);
+  return KX_OK;
+}
+
 // Lossy layer: linear ramp sigma_max d / L; PML: quadratic sigma_max (d/L)^2
 // (Sect. 4.1).
 template <typename T>

@@ -522,6 +522,7 @@ constexpr size_t SW_STAGE_FLOATS = 6 * (size_t)SW_TILE;           // one column 
 constexpr size_t SW_SMEM = SW_STAGES * SW_STAGE_FLOATS * sizeof(float);
 constexpr unsigned SW_WAIT_LIMIT = 1u << 22;                      // try_wait rounds of one wait
 static_assert(SW_STAGES == 4, "the wait parity below is (e >> 2) & 1");
+static_assert(SW_WAIT_LIMIT == KX_WAIT_SELFTEST_MAX_ROUNDS, "the self-test runs at most one wait's limit");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -802,13 +803,11 @@ static kx_status sweep_t(kx_ctx* c, int slot, int m) {
   const bool quad = f3 && (g.nx % 4) == 0;
   int nba = 0, nbs = 0;
   if (quad) {
-    // the attribute is set before the flag, so no thread (contexts of the
-    // multi-problem driver run on several) launches before it is in place
-    static std::atomic<int> smem_set{0};
-    if (!smem_set.load()) {
-      cudaFuncSetAttribute(k_sw_pass4s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SW_SMEM);
-      smem_set.store(1);
-    }
+    // per device, and before any launch (contexts of the multi-problem
+    // driver run on several host threads)
+    static SmemOptIn smem{};
+    const kx_status so = smem_opt_in(c, smem, (const void*)k_sw_pass4s, SW_SMEM);
+    if (so != KX_OK) return so;
     sw_grids(c, (const void*)k_sw_apply4, (const void*)k_sw_pass4s, SW_SMEM, 7, g.ncell / 4, &nba, &nbs);
   } else {
     sw_grids(c, (const void*)k_sw_apply<T, DIM, TableMat<T>>, (const void*)k_sw_pass<T, DIM, TableMat<T>>, 0,

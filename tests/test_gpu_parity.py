@@ -378,3 +378,28 @@ def test_multi_problem_driver_uneven_sizes():
     assert abs(inten[0, 1] - want) < 1e-9 * want
     for c in ctxs:
         c.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_create_from_material_ids(prec):
+    """krylov_expm_create_mat: a material id per cell (device uint8) and a
+    table of permittivities give the operator of the per-cell array they
+    expand to (checked against the oracle), and an id outside the table is
+    refused."""
+    grid = GRIDS["3d_pecz"]
+    ids = np.random.default_rng(7).integers(0, 3, size=grid.shape).astype(np.uint8)
+    table = np.array([1.0, 2.25, 4.0])
+    eps = table[ids]
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    ctx = Context(grid, None, precision=prec, krylov_dim=8,
+                  mat_id=torch.tensor(ids.reshape(-1), device="cuda"), eps_table=table)
+    op = yee.Operator(grid, eps)
+    v = S.random_vector(grid.nunk, 4)
+    for transpose in (False, True):
+        w = ctx.apply_A(dev(v, dt), transpose=transpose).cpu().numpy()
+        want = op.apply_T(v) if transpose else op.apply(v)
+        assert rel(w, want) < (1e-13 if prec == "fp64" else 1e-6)
+    ctx.close()
+    with pytest.raises(KxError, match="n_mat"):
+        Context(grid, None, precision=prec, krylov_dim=8,
+                mat_id=torch.tensor(ids.reshape(-1), device="cuda"), eps_table=table[:2])

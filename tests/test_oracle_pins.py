@@ -387,3 +387,19 @@ def test_plane_extraction_and_intensity():
         comp = y[(3 + q) * nc:(4 + q) * nc].reshape(8, 8, 8)
         np.testing.assert_array_equal(P[q], comp[5].reshape(-1))
     assert yee.intensity(g, y, (2, 5)) == float((P * P).sum())
+
+
+def test_plain_route_by_pieces():
+    """The augmented route taken one sub-interval at a time (the semigroup
+    property exp((s + t) L) = exp(s L) exp(t L)): its intermediate states are
+    the split1 solution at those times (eq. (split1), an independent route),
+    and a different balance eta of the phase entries gives the same y."""
+    sc = S.config_3d(n=8, fill=0.2)
+    A = yee.Operator(sc.grid, sc.eps_cell).matrix()
+    om = 0.9 * S.OMEGA0
+    T = 6.0
+    states = list(exact.y_plain_pieces(A, sc.g, om, T, 4, eta=float(np.abs(sc.g).sum())))
+    assert [k for k, _ in states] == [1, 2, 3, 4]
+    for k, y in states:
+        want = exact.y_split(A, sc.g, om, k * T / 4)
+        assert np.linalg.norm(y - want) < 1e-11 * np.linalg.norm(want)
