@@ -5,6 +5,7 @@
 // summed by the last block to finish.
 #include <atomic>
 
+#include "kx_eft.cuh"
 #include "kx_internal.cuh"
 #include "kx_reduce.cuh"
 
@@ -40,7 +41,8 @@ template <> __device__ __forceinline__ double2 vzero<double>() { return make_dou
 // Arnoldi pass B (step j): w <- w - sum_{i<=j} h_{ij} v_i (classical
 // Gram-Schmidt), h_{j+1,j} = ||w||, scale[j+1] = 1/h_{j+1,j}.  The stored
 // column stays unnormalised (delayed normalisation); a lucky breakdown
-// h_{j+1,j} <= tol * max_i ||A v_i|| stops the process.
+// h_{j+1,j} <= tol * max_i ||A v_i|| stops the process.  In FP32 the update
+// is compensated (kx_eft.cuh) and rounded once when the column is stored.
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS) k_pass_b(SlotSet<T> ss, int j, int64_t n, int64_t ld,
                                                     int ldh, int aug, double btol) {
@@ -59,6 +61,38 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_b(SlotSet<T> ss, int j, int64
   const int64_t nv = n / W;
   const V4* __restrict__ Vv = reinterpret_cast<const V4*>(s.V);
   const int64_t ldv = ld / W;
+  if constexpr (sizeof(T) == 4) {
+    const float4* __restrict__ Vf = reinterpret_cast<const float4*>(s.V);
+    float* __restrict__ wf = reinterpret_cast<float*>(w);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
+         q += (int64_t)gridDim.x * blockDim.x) {
+      float4 x = reinterpret_cast<const float4*>(wf)[q];
+      float4 lo = make_float4(0.f, 0.f, 0.f, 0.f);
+      int col = 0;
+      // eight independent column loads in flight per thread
+      for (; col + 8 <= ncol; col += 8) {
+        float4 v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = Vf[(int64_t)(col + t) * ldv + q];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) sub_fma4(x, lo, -(float)coef[col + t], v[t]);
+      }
+      for (; col < ncol; ++col) sub_fma4(x, lo, -(float)coef[col], Vf[(int64_t)col * ldv + q]);
+      x = make_float4(x.x + lo.x, x.y + lo.y, x.z + lo.z, x.w + lo.w);
+      reinterpret_cast<float4*>(wf)[q] = x;
+      nrm += (double)vdot(x);
+    }
+    for (int64_t e = nv * W + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      float x = wf[e], lo = 0.f;
+      for (int col = 0; col < ncol; ++col) sub_fma(x, lo, -(float)coef[col], (float)s.V[(int64_t)col * ld + e]);
+      x += lo;
+      wf[e] = x;
+      nrm += (double)x * (double)x;
+    }
+    block_partial(nrm, s.part, s.ps, FINB_COL);
+    return;
+  }
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
        q += (int64_t)gridDim.x * blockDim.x) {
     V4 x = reinterpret_cast<const V4*>(w)[q];

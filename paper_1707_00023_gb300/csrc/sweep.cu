@@ -35,6 +35,7 @@
 // (2 j + 5) n s for the two-pass form.
 #include <atomic>
 
+#include "kx_eft.cuh"
 #include "kx_internal.cuh"
 #include "kx_reduce.cuh"
 #include "kx_stencil.cuh"
@@ -362,9 +363,11 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_sw_apply4(Geo g, Slot<float> s,
 // each column the dots with the current y and x, then its removal from both.
 // FULL: all CH columns exist (no per-column test).  An inactive thread
 // (act false) removes nothing, so its x and y stay zero and so do its dots.
+// In FP32 x is compensated (x + xl, kx_eft.cuh); in FP64 xl is unused.
 template <typename T, int NC, int CH, bool FULL>
 __device__ __forceinline__ void sw_columns(const T* __restrict__ V, int64_t ld, int64_t nc, int64_t cell, int cb,
-                                           int j, const T* ch, const T* cc, bool act, T* x, T* y, T* pa, T* pb) {
+                                           int j, const T* ch, const T* cc, bool act, T* x, T* xl, T* y, T* pa,
+                                           T* pb) {
   T vv[CH][NC];
 #pragma unroll
   for (int k = 0; k < CH; ++k) {
@@ -387,7 +390,12 @@ __device__ __forceinline__ void sw_columns(const T* __restrict__ V, int64_t ld, 
       const T a = act ? ch[cb + k] : T(0), b = act ? cc[cb + k] : T(0);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        x[c] -= a * vv[k][c];
+        if constexpr (sizeof(T) == 4) {
+          sub_fma(x[c], xl[c], -a, vv[k][c]);
+        } else {
+          (void)xl;
+          x[c] -= a * vv[k][c];
+        }
         y[c] -= b * vv[k][c];
       }
     }
@@ -412,6 +420,7 @@ __global__ void __launch_bounds__(NTHREADS) k_sw_pass(Geo g, Slot<T> s, SwSlot w
     cc[i] = (T)(w.co->cp[i] * sc);
   }
   const T sp = (T)w.co->sprev, hjj = (T)w.co->hjj;
+  const T spl = (T)(w.co->sprev - (double)sp);
   __syncthreads();
   const T* __restrict__ t = (const T*)w.t;
   T* __restrict__ xout = s.V + (int64_t)j * ld;
@@ -419,27 +428,29 @@ __global__ void __launch_bounds__(NTHREADS) k_sw_pass(Geo g, Slot<T> s, SwSlot w
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nc; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t cell = base + threadIdx.x;
     const bool act = cell < nc;
-    T x[NC], y[NC];
+    T x[NC], xl[NC], y[NC];
     if (act) {
       const Cell q = make_cell(g, cell);
       T at[NC];
       stencil<T, DIM, 0>(g, t, mat, q, at);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        x[c] = sp * t[(int64_t)c * nc + cell];
+        const T tv = t[(int64_t)c * nc + cell];
+        x[c] = sp * tv;
+        xl[c] = sizeof(T) == 4 ? fma(spl, tv, fma(sp, tv, -x[c])) : T(0);
         y[c] = sp * at[c] - hjj * x[c];
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) x[c] = y[c] = T(0);
+      for (int c = 0; c < NC; ++c) x[c] = xl[c] = y[c] = T(0);
     }
     // an inactive thread reads cell 0 (in bounds), removes nothing and
     // contributes zero dots
     const int64_t cl = act ? cell : 0;
     for (int cb = 0; cb < j; cb += CH) {
       T pa[CH], pb[CH];
-      if (cb + CH <= j) sw_columns<T, NC, CH, true>(s.V, ld, nc, cl, cb, j, ch, cc, act, x, y, pa, pb);
-      else sw_columns<T, NC, CH, false>(s.V, ld, nc, cl, cb, j, ch, cc, act, x, y, pa, pb);
+      if (cb + CH <= j) sw_columns<T, NC, CH, true>(s.V, ld, nc, cl, cb, j, ch, cc, act, x, xl, y, pa, pb);
+      else sw_columns<T, NC, CH, false>(s.V, ld, nc, cl, cb, j, ch, cc, act, x, xl, y, pa, pb);
 #pragma unroll
       for (int k = 0; k < CH; ++k) {
         pa[k] = warp_sum(pa[k]);
@@ -461,6 +472,7 @@ __global__ void __launch_bounds__(NTHREADS) k_sw_pass(Geo g, Slot<T> s, SwSlot w
     if (act) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
+        x[c] += xl[c];   // the compensated column, rounded once (FP32; xl = 0 in FP64)
         xout[(int64_t)c * nc + cell] = x[c];
         xx += x[c] * x[c];
         xy += x[c] * y[c];
@@ -492,6 +504,16 @@ __global__ void __launch_bounds__(NTHREADS) k_sw_pass(Geo g, Slot<T> s, SwSlot w
 __device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
 __device__ __forceinline__ float4 join2(const float2& a, const float2& b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+// The compensated update of kx_eft.cuh (sub_fma), two lanes at a time in
+// packed FP32x2 operations: hi + lo <- hi + lo + nch v.
+__device__ __forceinline__ void sub_fma2(float2& hi, float2& lo, float2 nch, float2 v) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 s = __ffma2_rn(nch, v, hi);    // fl(hi + nch v)
+  const float2 d = __ffma2_rn(s, m1, hi);     // hi - s, exact when s is within a factor 2 of hi
+  lo = __fadd2_rn(lo, __ffma2_rn(nch, v, d)); // + the rounding error of s
+  hi = s;
+}
 
 // Warp sums of two values in a fixed order: lane l ends with the sum of
 // value (l >> 4) & 1, so lanes 0 and 16 hold the sums of v0 and v1.
@@ -619,7 +641,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s,
     ch[i] = (float)(w.co->hc[i] * sc);
     cc[i] = (float)(w.co->cp[i] * sc);
   }
-  const float sp = (float)w.co->sprev, hjj = (float)w.co->hjj;
+  const float sp = (float)w.co->sprev, spl = (float)(w.co->sprev - (double)sp);
+  const float hjj = (float)w.co->hjj;
   const int64_t nc = g.ncell, nq = nc >> 2;
   const int64_t ntiles = (nc + SW_TILE - 1) / SW_TILE;
   const int64_t mine = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -637,7 +660,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s,
     }
   const float* __restrict__ t = (const float*)w.t;
   float* __restrict__ xout = s.V + (int64_t)j * ld;
-  float4 x[6], y[6];
+  // x = hi + lo (compensated, kx_eft.cuh); y plain FP32 (it enters only the dots)
+  float4 x[6], xl[6], y[6];
   bool act = false, ok = true;
   int64_t c0 = 0, tile = blockIdx.x;
   int col = 0;
@@ -655,13 +679,16 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s,
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
           const float4 tv = ld4(t + c * nc + c0);
+          // x = (sp + spl) t exactly up to the rounding of lo
           x[c] = make_float4(sp * tv.x, sp * tv.y, sp * tv.z, sp * tv.w);
+          xl[c] = make_float4(fmaf(spl, tv.x, fmaf(sp, tv.x, -x[c].x)), fmaf(spl, tv.y, fmaf(sp, tv.y, -x[c].y)),
+                              fmaf(spl, tv.z, fmaf(sp, tv.z, -x[c].z)), fmaf(spl, tv.w, fmaf(sp, tv.w, -x[c].w)));
           y[c] = make_float4(sp * at[c].x - hjj * x[c].x, sp * at[c].y - hjj * x[c].y, sp * at[c].z - hjj * x[c].z,
                              sp * at[c].w - hjj * x[c].w);
         }
       } else {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) x[c] = y[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c = 0; c < 6; ++c) x[c] = xl[c] = y[c] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     if (col == j - 1) {
@@ -692,18 +719,23 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s,
       const float2 na = make_float2(-ch[col], -ch[col]), nb = make_float2(-cc[col], -cc[col]);
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
-        x[c] = join2(__ffma2_rn(na, lo2(vv[c]), lo2(x[c])), __ffma2_rn(na, hi2(vv[c]), hi2(x[c])));
+        float2 h0 = lo2(x[c]), h1 = hi2(x[c]), l0 = lo2(xl[c]), l1 = hi2(xl[c]);
+        sub_fma2(h0, l0, na, lo2(vv[c]));
+        sub_fma2(h1, l1, na, hi2(vv[c]));
+        x[c] = join2(h0, h1);
+        xl[c] = join2(l0, l1);
         y[c] = join2(__ffma2_rn(nb, lo2(vv[c]), lo2(y[c])), __ffma2_rn(nb, hi2(vv[c]), hi2(y[c])));
       }
     }
     const float r = warp_sum2(pa, pb, lane);
     if ((lane & 15) == 0) acc[warp][(lane >> 4) * j + col] += (double)r;
     if (col == j - 1) {
-      // the tile ends: store V_j = x, accumulate x.x, x.y, y.y
+      // the tile ends: store V_j = x (hi + lo rounded once), accumulate x.x, x.y, y.y
       float xx = 0.f, xy = 0.f, yy = 0.f;
       if (act) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
+          x[c] = make_float4(x[c].x + xl[c].x, x[c].y + xl[c].y, x[c].z + xl[c].z, x[c].w + xl[c].w);
           *reinterpret_cast<float4*>(xout + c * nc + c0) = x[c];
           xx += dot4(x[c], x[c]);
           xy += dot4(x[c], y[c]);
