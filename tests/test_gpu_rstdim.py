@@ -8,7 +8,14 @@ replaces each alphahat by its quintic Hermite interpolant on the sample
 grid (relative error about 1e-12 at the FP64 spacing, 1e-9 at the FP32 one);
 intermediate restarts amplify every rounding by the growth of alphahat (a
 few times on these cases), so FP64 is held to 1e-9 relative L2 and FP32 to
-3e-6 (three times the response accuracy target).
+the response accuracy target, 1e-6.
+
+Sources: a random field in the range of A (g = A r, r random, computed by
+the oracle).  A plain random field has a large curl-free part in the null
+space of A (sigma = 0 away from the layers), whose response grows like
+(1 - cos W T)/W; FP32 rounding in the curl turns that part into a spurious
+source, which puts the lowest frequency near 1.6e-6 whatever the Krylov
+dimension.  The benchmark's plane source has no such part.
 """
 import numpy as np
 import pytest
@@ -24,7 +31,7 @@ if not torch.cuda.is_available():
 from paper_1707_00023_gb300 import Context, KxError  # noqa: E402
 from paper_1707_00023_gb300._binding import KX_EINVAL, KX_ENOCONV  # noqa: E402
 
-TOL = {"fp64": 1e-9, "fp32": 3e-6}
+TOL = {"fp64": 1e-9, "fp32": 1e-6}
 
 
 def rel(a, b):
@@ -47,10 +54,15 @@ CASES = {
 FORMS = ["twopass", "sweep"]
 
 
+def range_source(grid, eps, seed):
+    """g = A r for a random r: a random source in the range of A."""
+    return yee.Operator(grid, eps).apply(S.masked_random_vector(grid, seed))
+
+
 def make(name):
     grid, m, T = CASES[name]
     eps = 1.0 + 3.0 * np.random.default_rng(11).random(grid.shape)
-    g = S.masked_random_vector(grid, 12)
+    g = range_source(grid, eps, 12)
     la = grid.layer_axis
     plane = (la, grid.n[la] - grid.layer_cells - 2)
     return grid, eps, g, m, T, plane
@@ -258,28 +270,32 @@ def test_full_size_3d64_T400_against_time_restarted_fp64(form):
     """The 64^3 benchmark configuration (m = 64, T = 400, 32 frequencies)
     by restart in dimension in FP32, against the FP64 time-restarted method
     (an independent algorithm, itself oracle-checked) on the first and last
-    frequency: plane fields within 3e-6."""
+    frequency: plane and full fields within 1e-6."""
     sc = S.config_3d(n=64, seed=1709, fill=0.3, T=400.0, m=64)
     oms = S.freq_list(32)
     ctx = Context(sc.grid, sc.eps_cell, precision="fp32", krylov_dim=64, max_freqs=32, rst_samples=4096,
                   arnoldi=form)
-    a = ctx.response_restart_dim(dev(sc.g, "fp32"), oms, sc.T, rtol=1e-7, plane=sc.plane)
+    a = ctx.response_restart_dim(dev(sc.g, "fp32"), oms, sc.T, rtol=1e-7, plane=sc.plane, want_full=True)
     ctx.close()
     assert np.all(a["resid"] <= 1e-7)
     ctx = Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=64, max_freqs=2, batch=2)
-    b = ctx.response_at_freqs(dev(sc.g, "fp64"), oms[[0, 31]], sc.T, rtol=1e-11, method="plain", plane=sc.plane)
+    b = ctx.response_at_freqs(dev(sc.g, "fp64"), oms[[0, 31]], sc.T, rtol=1e-11, method="plain", plane=sc.plane,
+                              want_full=True)
     ctx.close()
     for k, f in enumerate((0, 31)):
-        assert rel(a["E_plane"][f].double().cpu().numpy(), b["E_plane"][k].cpu().numpy()) < 3e-6
+        assert rel(a["E_plane"][f].double().cpu().numpy(), b["E_plane"][k].cpu().numpy()) < 1e-6
+        assert rel(a["Y"][f].double().cpu().numpy(), b["Y"][k].cpu().numpy()) < 1e-6
 
 
 def test_full_size_3d128_T400_default_against_time_restarted_fp64():
-    """The default benchmark configuration (3D 128^3, m = 64, T = 400, 32
-    frequencies, two basis slots, the default Arnoldi form: the single sweep
-    on this grid) in FP32, against the FP64 time-restarted method on the
-    first and last frequency: plane fields within 1e-6 (the accuracy the
-    benchmark metric is stated at), full fields within 3e-6."""
-    sc = S.config_3d(n=128, seed=1709, fill=0.3, T=400.0, m=64)
+    """The default benchmark configuration itself (3D 128^3, the benchmark's
+    own medium, m = 64, T = 400, 32 frequencies, two basis slots, the
+    default Arnoldi form: the single sweep on this grid) in FP32: every
+    frequency against the FP64 path of the same method, and the first and
+    last against the FP64 time-restarted method (an independent algorithm,
+    itself oracle-checked); plane and full fields within 1e-6, the accuracy
+    the benchmark metric is stated at."""
+    sc = S.config_3d(n=128, seed=1710, fill=0.3, T=400.0, m=64)
     oms = S.freq_list(32)
     ctx = Context(sc.grid, sc.eps_cell, precision="fp32", krylov_dim=64, max_freqs=32, batch=2, rst_samples=4096)
     ctx.set_timing(True)
@@ -288,6 +304,14 @@ def test_full_size_3d128_T400_default_against_time_restarted_fp64():
     ctx.close()
     assert kt["sweep"]["launches"] > 0 and kt["pass_a"]["launches"] == 0
     assert np.all(a["resid"] <= 1e-7)
+    ctx = Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=64, max_freqs=32, batch=2, rst_samples=16384)
+    r = ctx.response_restart_dim(dev(sc.g, "fp64"), oms, sc.T, rtol=1e-11, plane=sc.plane, want_full=True)
+    ctx.close()
+    for f in range(32):
+        assert float(torch.linalg.norm(a["Y"][f].double() - r["Y"][f]) / torch.linalg.norm(r["Y"][f])) < 1e-6
+        assert float(torch.linalg.norm(a["E_plane"][f].double() - r["E_plane"][f])
+                     / torch.linalg.norm(r["E_plane"][f])) < 1e-6
+    del r
     ya = a["Y"][[0, 31]].double().cpu().numpy()
     del a["Y"]
     ctx = Context(sc.grid, sc.eps_cell, precision="fp64", krylov_dim=64, max_freqs=2, batch=2)
@@ -296,4 +320,4 @@ def test_full_size_3d128_T400_default_against_time_restarted_fp64():
     ctx.close()
     for k, f in enumerate((0, 31)):
         assert rel(a["E_plane"][f].double().cpu().numpy(), b["E_plane"][k].cpu().numpy()) < 1e-6
-        assert rel(ya[k], b["Y"][k].cpu().numpy()) < 3e-6
+        assert rel(ya[k], b["Y"][k].cpu().numpy()) < 1e-6

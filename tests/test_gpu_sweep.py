@@ -140,14 +140,15 @@ def test_sweep_launches_two_kernels_a_step():
     assert kt["pass_a"]["launches"] == 0 and kt["pass_b"]["launches"] == 0
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 3e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-6)])
 @pytest.mark.parametrize("nx", [14, 16])
 def test_restart_dim_forms_agree(prec, tol, nx):
     """Restart in Krylov dimension with either form, against the exact
     solution and against each other (nx = 16: the FP32 quad kernels)."""
     grid = S.Grid(3, (nx, 11, 13), (S.PERIODIC, S.PERIODIC, S.PEC), 2, 2, 1.0)
     eps = eps_of(grid, 11)
-    g = S.masked_random_vector(grid, 12)
+    # a random source in the range of A (no curl-free part, see test_gpu_rstdim)
+    g = yee.Operator(grid, eps).apply(S.masked_random_vector(grid, 12))
     oms = S.freq_list(3)
     T = 20.0
     dt = torch.float64 if prec == "fp64" else torch.float32
@@ -162,7 +163,7 @@ def test_restart_dim_forms_agree(prec, tol, nx):
     A = yee.Operator(grid, eps).matrix()
     for f, W in enumerate(oms):
         want = exact.y_plain(A, g, W, T)
-        assert rel(Y["sweep"][f], want) < (1e-9 if prec == "fp64" else 3e-6)
+        assert rel(Y["sweep"][f], want) < (1e-9 if prec == "fp64" else 1e-6)
         assert rel(Y["sweep"][f], Y["twopass"][f]) < tol
 
 
