@@ -85,6 +85,14 @@ WORKLOADS = {
     # restart for its 4 frequencies)
     "uneven48_4f_rst": dict(kind="uneven", count=48, seed=1711, T=400.0, m=64, nfreq=4, prec="fp32",
                             method="rstdim", rtol=1e-7, threads=8, rst_samples=4096),
+    # 48 instances with sizes from {32, 36, ..., 96}^3 (x a multiple of 4), by
+    # restart in Krylov dimension: batched (one launch per Arnoldi phase for
+    # all instances, autotuned split) and, for comparison, the host-thread
+    # driver on the same instances
+    "uneven48_4f_rst_batch": dict(kind="uneven", count=48, seed=1711, T=400.0, m=64, nfreq=4, prec="fp32",
+                                  method="rstdim", rtol=1e-7, rst_samples=4096, step=4, batched=True),
+    "uneven48x4_4f_rst_threads": dict(kind="uneven", count=48, seed=1711, T=400.0, m=64, nfreq=4, prec="fp32",
+                                      method="rstdim", rtol=1e-7, threads=8, rst_samples=4096, step=4),
     # adjoint: 3D 96^3, 8 frequencies, gradient of the summed output-plane intensity
     "adjoint3d96_8f": dict(kind="adjoint", dim=3, n=96, seed=1712, fill=0.3, T=400.0, m=64, nfreq=8,
                            prec="fp32", method="plain", rtol=1e-7, checkpoints=128),
@@ -334,7 +342,8 @@ def run_uneven(args, w):
 
     rank, world, local, dist = dist_setup(args.gpus)
     t0 = time.perf_counter()
-    scs = S.config_uneven(count=w["count"], seed=w["seed"] + rank, T=w["T"], m=w["m"], nfreq=w["nfreq"])
+    scs = S.config_uneven(count=w["count"], seed=w["seed"] + rank, T=w["T"], m=w["m"], nfreq=w["nfreq"],
+                          step=w.get("step", 1))
     t_gen = time.perf_counter() - t0
     dt = torch.float64 if w["prec"] == "fp64" else torch.float32
     ctxs, gs = [], []
@@ -347,15 +356,27 @@ def run_uneven(args, w):
     oms = np.stack([sc.omegas for sc in scs])
     planes = np.array([sc.plane for sc in scs])
     main_stream = torch.cuda.current_stream()
-    launches0 = sum(c.stats()["kernel_launches"] for c in ctxs)
     res = {}
+    batch = None
+    if w.get("batched"):
+        from paper_1707_00023_gb300 import Batch
+        batch = Batch(ctxs)
+        tune = batch.info()
 
-    def step():
-        res["out"] = response_multi(ctxs, gs, oms, w["T"], rtol=w["rtol"], method=w["method"], planes=planes,
-                                    nthreads=w["threads"])
+        def step():
+            res["out"] = batch.response(gs, oms, w["T"], rtol=w["rtol"], planes=planes)
+    else:
+        def step():
+            res["out"] = response_multi(ctxs, gs, oms, w["T"], rtol=w["rtol"], method=w["method"], planes=planes,
+                                        nthreads=w["threads"])
 
+    def launch_count():
+        n = sum(c.stats()["kernel_launches"] for c in ctxs)
+        return n + (batch.info()["batched_launches"] if batch is not None else 0)
+
+    launches0 = launch_count()
     dev_ms, wall, clk = timed_steps(args, dist, step, main_stream)
-    launches = sum(c.stats()["kernel_launches"] for c in ctxs) - launches0
+    launches = launch_count() - launches0
     # device events on the current stream do not order the instance streams;
     # the wall clock around the synchronised call is the job time here
     job_s = barrier_max(dist, wall)
@@ -369,12 +390,17 @@ def run_uneven(args, w):
                 "config": {"workload": args.workload, "method": w["method"], "instances": len(scs),
                            "sizes_min_max": [min(sizes), max(sizes)],
                            "unknowns_total": int(sum(sc.grid.nunk for sc in scs)), "nfreq_each": w["nfreq"],
-                           "T": w["T"], "krylov_dim": w["m"], "host_threads": w["threads"],
+                           "T": w["T"], "krylov_dim": w["m"],
+                           "driver": "batched launches" if batch is not None else f"{w['threads']} host threads",
                            "timing": "wall clock around the synchronised multi-problem call",
                            "media_generation_s": round(t_gen, 1)},
                 "gpu_launches": launches, "clocks": clk, "roofline": None, "cpu_baseline": None,
                 "e2e": None}
+        if batch is not None:
+            line["autotune"] = tune
         print(json.dumps(line), flush=True)
+    if batch is not None:
+        batch.close()
     for c in ctxs:
         c.close()
 

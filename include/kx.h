@@ -328,6 +328,60 @@ kx_status response_at_freqs_multi(kx_ctx* const* ctxs, int nctx, const void* con
                                   const double* omegas, int nfreq, double T, double rtol, int method,
                                   const int* planes, double* intensity, double* err_est, int nthreads);
 
+/* Batched restart in Krylov dimension for many independent problems (the
+ * uneven batch of Sect. 4's use case: scatterer instances of different sizes,
+ * a few frequencies each).  Each problem keeps its own context; the Arnoldi
+ * process of every restart (Sect. 3.2) runs for all problems together, one
+ * launch per phase whose blocks a table splits between the problems, and
+ * each problem's per-frequency projected work (Fig. alg:rst steps (2), (3))
+ * runs on its context's auxiliary stream beside the next batched Arnoldi
+ * process.  Results equal response_restart_dim on each problem up to the
+ * order of the block reductions.
+ *
+ * kx_batch_create: ctxs are nctx distinct contexts, each 3D, KX_FP32, the
+ * lossy layer, n[0] a multiple of 4, batch >= 2, rst_samples > 0, and all
+ * with the same krylov_dim; they stay owned by the caller and must outlive
+ * the batch, and must not be used by other calls while a batched call runs.
+ * cuda_stream: the stream of the batched launches (or KX_OWN_STREAM).
+ * Creation allocates a small table and chooses how each launch is split
+ * (an autotuner times an Arnoldi process of min(12, krylov_dim) steps of the whole batch for each
+ * candidate granularity -- sweep tiles per block 1..16, stencil rounds per
+ * apply thread 1..4 -- and keeps the fastest; the choice is cached per size
+ * class, the multiset of the problems' grids, for the rest of the process).
+ * The timing runs overwrite basis slot 0 of every context.
+ * Errors: KX_EINVAL (arguments, a context that does not qualify), KX_ENOMEM,
+ * KX_ECUDA; text by kx_batch_last_error(NULL). */
+typedef struct kx_batch kx_batch;
+typedef struct {
+  int problems;
+  int sweep_tiles_per_block;    /* the autotuner's choice                      */
+  int apply_rounds_per_thread;  /* the autotuner's choice                      */
+  int sweep_blocks;             /* blocks of one batched sweep launch          */
+  int apply_blocks;             /* blocks of one batched apply launch          */
+  int from_cache;               /* 1: the choice came from an earlier batch    */
+  double tune_ms;               /* time the timing runs took (0 if cached)     */
+  int64_t batched_launches;     /* batched Arnoldi launches so far             */
+} kx_batch_info;
+kx_status kx_batch_create(kx_ctx* const* ctxs, int nctx, void* cuda_stream, kx_batch** out);
+kx_status kx_batch_destroy(kx_batch* batch);
+kx_status kx_batch_get_info(const kx_batch* batch, kx_batch_info* out);
+const char* kx_batch_last_error(const kx_batch* batch);
+
+/* Responses of every problem of a batch by restart in Krylov dimension (as
+ * response_restart_dim, with dt_sample = 0).
+ *   d_g      : nctx device sources (problem i's grid, FP32).
+ *   omegas   : host nctx x nfreq, row i = problem i's frequencies
+ *              (nfreq <= every context's max_freqs).
+ *   planes   : host nctx x 2 output planes {axis, index}.
+ *   intensity, resid: host nctx x nfreq (or NULL), as for
+ *              response_restart_dim.  restarts: host nctx x nfreq int (or NULL).
+ * Synchronises the batch's stream.  KX_ENOCONV when some frequency has not
+ * stopped after max_restarts restarts (0: the default cap per problem);
+ * KX_ETIMEOUT when a bounded device wait ran out. */
+kx_status response_restart_dim_batch(kx_batch* batch, const void* const* d_g, const double* omegas, int nfreq,
+                                     double T, double rtol, int max_restarts, const int* planes, double* intensity,
+                                     double* resid, int* restarts);
+
 /* Counters; kx_reset_stats zeroes them. */
 kx_status kx_get_stats(const kx_ctx* ctx, kx_stats* out);
 kx_status kx_reset_stats(kx_ctx* ctx);

@@ -29,7 +29,8 @@ EXPORTS = ["krylov_expm_create", "krylov_expm_create_mat", "krylov_expm_destroy"
            "response_at_freqs", "kx_get_stats", "kx_reset_stats", "kx_set_timing",
            "kx_kernel_times", "kx_last_error", "kx_arnoldi_noalloc", "kx_noalloc_last_error",
            "adjoint_response_grad", "kx_set_permittivity", "response_at_freqs_multi", "kx_stream",
-           "response_restart_dim", "kx_wait_selftest"]
+           "response_restart_dim", "kx_wait_selftest", "kx_batch_create", "kx_batch_destroy",
+           "kx_batch_get_info", "kx_batch_last_error", "response_restart_dim_batch"]
 KCLASSES = ["pass_a", "pass_b", "restart", "projected", "zupdate", "apply", "cascade", "sweep", "swapply"]
 # Arnoldi forms (kx_desc.arnoldi_form)
 ARNOLDI_FORMS = {"default": 0, "twopass": 1, "sweep": 2}
@@ -52,6 +53,13 @@ class Desc(ctypes.Structure):
 
 class KernelTime(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("bytes", ctypes.c_double), ("launches", ctypes.c_int64)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("problems", ctypes.c_int), ("sweep_tiles_per_block", ctypes.c_int),
+                ("apply_rounds_per_thread", ctypes.c_int), ("sweep_blocks", ctypes.c_int),
+                ("apply_blocks", ctypes.c_int), ("from_cache", ctypes.c_int), ("tune_ms", ctypes.c_double),
+                ("batched_launches", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):
@@ -107,8 +115,16 @@ def load_library(path: Optional[str] = None):
     lib.kx_noalloc_last_error.argtypes = []
     lib.kx_wait_selftest.argtypes = [vp, ctypes.c_uint]
     lib.kx_noalloc_last_error.restype = ctypes.c_char_p
+    lib.kx_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
+    lib.kx_batch_destroy.argtypes = [vp]
+    lib.kx_batch_get_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
+    lib.kx_batch_last_error.argtypes = [vp]
+    lib.kx_batch_last_error.restype = ctypes.c_char_p
+    lib.response_restart_dim_batch.argtypes = [vp, ctypes.POINTER(vp), dp, ctypes.c_int, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_int, ip, dp, dp, ip]
     for name in EXPORTS:
-        if name not in ("kx_num_unknowns", "kx_last_error", "kx_noalloc_last_error", "kx_stream"):
+        if name not in ("kx_num_unknowns", "kx_last_error", "kx_noalloc_last_error", "kx_stream",
+                        "kx_batch_last_error"):
             getattr(lib, name).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -409,3 +425,58 @@ def response_multi(ctxs, gs, omegas, T, rtol=1e-8, method="plain", planes=None, 
     if st != KX_OK:
         raise KxError(st, lib.kx_last_error(None).decode())
     return inten, err
+
+
+class Batch:
+    """Many independent problems solved together by restart in Krylov
+    dimension (``kx_batch_create`` / ``response_restart_dim_batch``): one
+    launch per Arnoldi phase serves every problem.  ``ctxs``: 3D FP32
+    Contexts (n[0] a multiple of 4, batch >= 2, rst_samples > 0, one
+    krylov_dim); they must outlive the Batch.  ``stream``: a torch CUDA
+    stream, or "own"."""
+
+    def __init__(self, ctxs, stream="own"):
+        import torch
+        self.lib = load_library()
+        self.ctxs = list(ctxs)
+        own = isinstance(stream, str) and stream == "own"
+        sarg = ctypes.c_void_p(-1) if own else ctypes.c_void_p(stream.cuda_stream)
+        hs = (ctypes.c_void_p * len(self.ctxs))(*[c.h for c in self.ctxs])
+        h = ctypes.c_void_p()
+        st = self.lib.kx_batch_create(hs, len(self.ctxs), sarg, ctypes.byref(h))
+        if st != KX_OK:
+            raise KxError(st, self.lib.kx_batch_last_error(None).decode())
+        self.h = h
+
+    def info(self):
+        i = BatchInfo()
+        self.lib.kx_batch_get_info(self.h, ctypes.byref(i))
+        return {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+
+    def response(self, gs, omegas, T, rtol=1e-7, max_restarts=0, planes=None, allow_noconv=False):
+        """(intensity, resid, restarts), each (nproblems, nfreq)."""
+        n = len(self.ctxs)
+        om = np.ascontiguousarray(np.asarray(omegas, np.float64).reshape(n, -1))
+        nf = om.shape[1]
+        pl = np.ascontiguousarray(np.asarray(planes, np.int32).reshape(n, 2))
+        gp = (ctypes.c_void_p * n)(*[c._vec(g, "g").value for c, g in zip(self.ctxs, gs)])
+        inten = np.zeros((n, nf))
+        res = np.zeros((n, nf))
+        rst = np.zeros((n, nf), np.int32)
+        st = self.lib.response_restart_dim_batch(self.h, gp, _dptr(om), nf, float(T), float(rtol), int(max_restarts),
+                                                 pl.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(inten),
+                                                 _dptr(res), rst.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        if not (allow_noconv and st == KX_ENOCONV) and st != KX_OK:
+            raise KxError(st, self.lib.kx_batch_last_error(self.h).decode())
+        return inten, res, rst
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.kx_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libkx.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["stencil.cu", "linalg.cu", "projected.cu", "api.cu", "noalloc.cu", "adjoint.cu", "rstdim.cu", "sweep.cu"]
+SOURCES = ["stencil.cu", "linalg.cu", "projected.cu", "api.cu", "noalloc.cu", "adjoint.cu", "rstdim.cu", "sweep.cu",
+           "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-Xptxas", "-O3"]

@@ -130,6 +130,8 @@ constexpr int RST_MATS = RST_OFF_SC + 8;
 // Single-sweep Arnoldi (sweep.cu): reduced partial columns of the last
 // pass, and the coefficients the next sweep applies.  One record per slot.
 constexpr int SWCOLS = 2 * MMAX + 3;   // dots against t2 and t1 per column, x.x, x.y, y.y
+constexpr int SW_RED = 16;             // blocks in front of an apply pass (from step 1) that finalise the step
+constexpr int SW_TILE = 4 * NTHREADS;  // cells of one tile of the staged sweep (a quad a thread)
 struct SwCoef {
   double tot[SWCOLS];   // reduced columns of the last sweep (step 0: v_0 . A v_0, ||A v_0||^2)
   double hc[MMAX + 1];  // h_{i,j-1}, i < j: the column the sweep S_j removes from A v_{j-1}
@@ -148,6 +150,20 @@ struct SwSlot {
   double* G;      // (MMAX+1) x (MMAX+1) Gram matrix v_i . v_k, column-major
   SwCoef* co;
   void* t;        // one vector: A V_{j-1} (shared by the slots: one process runs at a time)
+};
+
+// One problem of a batch (kx_batch): what its single-sweep Arnoldi kernels
+// need, for both basis slots, and its block ranges in the batched launches
+// (the apply launch's blocks [a0, a0 + na), the sweep launch's [s0, s0 + ns)).
+struct SwInst {
+  Geo g;
+  Slot<float> s[2];
+  SwSlot w[2];
+  const float* ie;
+  const float* sig2;
+  int64_t ld;
+  int ldh;
+  int a0, na, s0, ns;
 };
 
 struct Material {
@@ -288,6 +304,13 @@ kx_status launch_rst_nextvec(kx_ctx* c, cudaStream_t st, int from, int to);
 // sweep.cu: m steps of the single-sweep Arnoldi process on basis slot
 // `slot`, from its column 0 as set by launch_norm_init (non-augmented)
 kx_status sweep_arnoldi(kx_ctx* c, int slot, int m);
+// the same for every problem of a batch at once (3D FP32, nx % 4 == 0): one
+// launch per Arnoldi phase; tab/aoff/soff device copies of the instance
+// table and of the block offsets (n + 1 entries each), na/ns the launch totals
+kx_status sweep_arnoldi_batch(kx_ctx* c0, cudaStream_t st, const SwInst* tab, const int* aoff, const int* soff, int n,
+                              int na, int ns, int slot, int m, int64_t* launches);
+size_t sweep_smem_bytes();
+const void* sweep_batch_kernel();
 // the bounded mbarrier wait of the sweep on a barrier nothing completes
 kx_status launch_wait_selftest(kx_ctx* c, unsigned rounds, int* d_status);
 

@@ -33,6 +33,21 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
   return am_last;
 }
 
+// Block sum of one double per thread, written to part[col * ps + bid].
+__device__ __forceinline__ void block_partial_at(double x, double* part, int ps, int col, int bid) {
+  __shared__ double red[NWARPS];
+  x = warp_sum(x);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < NWARPS; ++w) t += red[w];
+    part[(int64_t)col * ps + bid] = t;
+  }
+  __syncthreads();
+}
+
 // Block sum of one double per thread, written to part[col * ps + blockIdx.x].
 __device__ __forceinline__ void block_partial(double x, double* part, int ps, int col) {
   __shared__ double red[NWARPS];

@@ -229,12 +229,11 @@ __device__ __forceinline__ bool last_of(unsigned* counter, unsigned count) {
 // Gram-row products uh, uc of rows i < j (one warp a row); the last of these
 // blocks finalises step j.  The stencil blocks behind them read none of it,
 // so the finalisation runs beside the stencil instead of after it.
-constexpr int SW_RED = 16;
 template <typename T>
 __device__ __forceinline__ void sw_reduce_fin(const Slot<T>& s, const SwSlot& w, int j, int ldh, int nbs,
-                                              double btol) {
+                                              double btol, int bid) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * NWARPS + warp;
+  const int gw = bid * NWARPS + warp;
   for (int col = gw; col < 2 * j + 3; col += SW_RED * NWARPS) {
     const double* p = w.part + (int64_t)col * w.ps;
     double x = 0.0;
@@ -263,15 +262,16 @@ __device__ __forceinline__ void sw_reduce_fin(const Slot<T>& s, const SwSlot& w,
 }
 
 // Step 0, at the end of apply pass K_0: the block partials of its dots
-// (d0 = V_0 . t, d1 = t . t); the last block reduces them and finalises.
+// (d0 = V_0 . t, d1 = t . t); the last of the nblk blocks reduces them and
+// finalises (bid: this block's index among them).
 template <typename T>
 __device__ __forceinline__ void sw_apply_tail0(const Slot<T>& s, const SwSlot& w, int ldh, double btol, double d0,
-                                               double d1) {
-  block_partial(d0, w.part, w.ps, 0);
-  block_partial(d1, w.part, w.ps, 1);
-  if (!last_of(&w.co->counter, gridDim.x)) return;
+                                               double d1, int bid, int nblk) {
+  block_partial_at(d0, w.part, w.ps, 0, bid);
+  block_partial_at(d1, w.part, w.ps, 1, bid);
+  if (!last_of(&w.co->counter, (unsigned)nblk)) return;
   for (int col = 0; col < 2; ++col) {
-    const double x = block_column_sum(w.part, w.ps, col, gridDim.x);
+    const double x = block_column_sum(w.part, w.ps, col, nblk);
     if (threadIdx.x == 0) w.co->tot[col] = x;
   }
   __syncthreads();
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(NTHREADS) k_sw_apply(Geo g, Slot<T> s, SwSlot 
   constexpr int NC = ncomp_of(DIM);
   const int R = j >= 1 ? SW_RED : 0;
   if ((int)blockIdx.x < R) {
-    sw_reduce_fin<T>(s, w, j, ldh, nbs, btol);
+    sw_reduce_fin<T>(s, w, j, ldh, nbs, btol, blockIdx.x);
     return;
   }
   const T* __restrict__ v = s.V + (int64_t)j * ld;
@@ -316,29 +316,29 @@ __global__ void __launch_bounds__(NTHREADS) k_sw_apply(Geo g, Slot<T> s, SwSlot 
     }
   }
   pdl_trigger();
-  if (j == 0) sw_apply_tail0<T>(s, w, ldh, btol, d0, d1);
+  if (j == 0) sw_apply_tail0<T>(s, w, ldh, btol, d0, d1, blockIdx.x, gridDim.x);
 }
 
 // Apply pass K_j, 3D FP32, one quad of x-cells a thread (nx % 4 == 0).
 // Three resident blocks per SM (80 registers, a small spill): the stencil is
 // latency-bound, and against two blocks (128 registers) the apply pass took
 // 77 instead of 97 ms a step at 128^3 and 41.5 instead of 49 at 96^3.
-__global__ void __launch_bounds__(NTHREADS, 3) k_sw_apply4(Geo g, Slot<float> s, SwSlot w, int j, int64_t ld,
-                                                       const float* __restrict__ ie, const float* __restrict__ sig2,
-                                                       int ldh, int nbs, double btol) {
-  pdl_wait();
-  if (s.st->done || s.st->retired) return;
+// The body takes its block index among the launch's blocks for this slot
+// (bid of nblk), so that one launch can serve several problems.
+__device__ __forceinline__ void sw_apply4_body(const Geo& g, const Slot<float>& s, const SwSlot& w, int j, int64_t ld,
+                                               const float* __restrict__ ie, const float* __restrict__ sig2, int ldh,
+                                               int nbs, double btol, int bid, int nblk) {
   const int R = j >= 1 ? SW_RED : 0;
-  if ((int)blockIdx.x < R) {
-    sw_reduce_fin<float>(s, w, j, ldh, nbs, btol);
+  if (bid < R) {
+    sw_reduce_fin<float>(s, w, j, ldh, nbs, btol, bid);
     return;
   }
   const float* __restrict__ v = s.V + (int64_t)j * ld;
   float* __restrict__ t = (float*)w.t;
   const int64_t nc = g.ncell, nq = nc >> 2;
   double d0 = 0.0, d1 = 0.0;
-  for (int64_t q4 = (int64_t)(blockIdx.x - R) * blockDim.x + threadIdx.x; q4 < nq;
-       q4 += (int64_t)(gridDim.x - R) * blockDim.x) {
+  for (int64_t q4 = (int64_t)(bid - R) * blockDim.x + threadIdx.x; q4 < nq;
+       q4 += (int64_t)(nblk - R) * blockDim.x) {
     const Quad qd = make_quad(g, q4);
     float4 o[6];
     stencil_quad(g, v, ie, sig2, qd, o);
@@ -356,7 +356,15 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_sw_apply4(Geo g, Slot<float> s,
     }
   }
   pdl_trigger();
-  if (j == 0) sw_apply_tail0<float>(s, w, ldh, btol, d0, d1);
+  if (j == 0) sw_apply_tail0<float>(s, w, ldh, btol, d0, d1, bid, nblk);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 3) k_sw_apply4(Geo g, Slot<float> s, SwSlot w, int j, int64_t ld,
+                                                       const float* __restrict__ ie, const float* __restrict__ sig2,
+                                                       int ldh, int nbs, double btol) {
+  pdl_wait();
+  if (s.st->done || s.st->retired) return;
+  sw_apply4_body(g, s, w, j, ld, ie, sig2, ldh, nbs, btol, blockIdx.x, gridDim.x);
 }
 
 // Loads and arithmetic of CH basis columns cb .. cb+CH-1 for one cell: for
@@ -538,7 +546,6 @@ __device__ __forceinline__ float warp_sum2(float v0, float v1, int lane) {
 // (measured at 128^3: 0.79 of the measured copy bandwidth, staged 0.84).
 // Every wait is bounded: when one runs out the block records KX_ETIMEOUT,
 // waits (bounded again) for its own copies and returns.
-constexpr int SW_TILE = 4 * NTHREADS;                             // cells a tile
 constexpr int SW_STAGES = 4;                                      // buffers in the ring (a power of 2)
 constexpr size_t SW_STAGE_FLOATS = 6 * (size_t)SW_TILE;           // one column of a tile
 constexpr size_t SW_SMEM = SW_STAGES * SW_STAGE_FLOATS * sizeof(float);
@@ -616,19 +623,20 @@ __device__ __forceinline__ void sw_issue(const Slot<float>& s, int64_t ld, int64
 struct SwCursor {
   int64_t tile;
   int col;
+  int stride;   // blocks of the block's problem: the tile stride
   __device__ __forceinline__ void next(int j) {
     if (++col == j) {
       col = 0;
-      tile += gridDim.x;
+      tile += stride;
     }
   }
 };
 
-__global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s, SwSlot w, int j, int64_t ld,
-                                                          const float* __restrict__ ie,
-                                                          const float* __restrict__ sig2) {
-  pdl_wait();
-  if (s.st->done || s.st->retired) return;
+// The body takes its block index among the launch's blocks for this slot
+// (bid of nblk), so that one launch can serve several problems.
+__device__ __forceinline__ void sw_pass4s_body(const Geo& g, const Slot<float>& s, const SwSlot& w, int j, int64_t ld,
+                                               const float* __restrict__ ie, const float* __restrict__ sig2, int bid,
+                                               int nblk) {
   extern __shared__ __align__(128) unsigned char sw_dyn[];
   float* ring = reinterpret_cast<float*>(sw_dyn);
   __shared__ __align__(8) uint64_t full[SW_STAGES];
@@ -645,14 +653,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s,
   const float hjj = (float)w.co->hjj;
   const int64_t nc = g.ncell, nq = nc >> 2;
   const int64_t ntiles = (nc + SW_TILE - 1) / SW_TILE;
-  const int64_t mine = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t mine = (int64_t)bid < ntiles ? (ntiles - 1 - bid) / nblk + 1 : 0;
   const int64_t E = mine * j;
   if (threadIdx.x == 0) {
     for (int b = 0; b < SW_STAGES; ++b) mbar_init(&full[b], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  SwCursor cur{(int64_t)blockIdx.x, 0};   // the next element to issue (thread 0)
+  SwCursor cur{(int64_t)bid, 0, nblk};   // the next element to issue (thread 0)
   if (threadIdx.x == 0)
     for (int64_t e = 0; e < E && e < SW_STAGES; ++e) {
       sw_issue(s, ld, nc, cur.tile, cur.col, (int)e, ring, full);
@@ -663,7 +671,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s,
   // x = hi + lo (compensated, kx_eft.cuh); y plain FP32 (it enters only the dots)
   float4 x[6], xl[6], y[6];
   bool act = false, ok = true;
-  int64_t c0 = 0, tile = blockIdx.x;
+  int64_t c0 = 0, tile = bid;
   int col = 0;
   for (int64_t e = 0; e < E; ++e) {
     if (col == 0) {
@@ -693,7 +701,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s,
     }
     if (col == j - 1) {
       // the tile's last column: prefetch the next tile's stencil inputs
-      const int64_t qn = (tile + gridDim.x) * NTHREADS + threadIdx.x;
+      const int64_t qn = (tile + nblk) * NTHREADS + threadIdx.x;
       if (qn < nq) prefetch_quad(g, t, ie, make_quad(g, qn));
     }
     const int b = (int)(e & (SW_STAGES - 1));
@@ -768,7 +776,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s,
     }
     if (++col == j) {
       col = 0;
-      tile += gridDim.x;
+      tile += nblk;
     }
   }
   pdl_trigger();
@@ -777,8 +785,16 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s,
     double tsum = 0.0;
 #pragma unroll
     for (int q = 0; q < NWARPS; ++q) tsum += acc[q][c2];
-    w.part[(int64_t)c2 * w.ps + blockIdx.x] = tsum;
+    w.part[(int64_t)c2 * w.ps + bid] = tsum;
   }
+}
+
+__global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s(Geo g, Slot<float> s, SwSlot w, int j, int64_t ld,
+                                                          const float* __restrict__ ie,
+                                                          const float* __restrict__ sig2) {
+  pdl_wait();
+  if (s.st->done || s.st->retired) return;
+  sw_pass4s_body(g, s, w, j, ld, ie, sig2, blockIdx.x, gridDim.x);
 }
 
 // Finalisation after the last sweep S_m (one block): beta_{m-1}, scale_m,
@@ -793,10 +809,117 @@ __global__ void __launch_bounds__(NTHREADS) k_sw_last(Slot<T> s, SwSlot w, int m
   sw_fin<T>(s, w.co, w.G, m, ldh, btol, 1);
 }
 
+// ---------------------------------------------------------------------------
+// Batched forms: one launch serves every problem of a batch.  Block b of a
+// launch belongs to problem i with off[i] <= b < off[i + 1] and runs that
+// problem's body as its block b - off[i] of off[i + 1] - off[i]; the
+// problem's record is copied to shared memory once per block.
+__device__ __forceinline__ int inst_of(const int* __restrict__ off, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void load_inst(SwInst& dst, const SwInst* __restrict__ tab, int i) {
+  static_assert(sizeof(SwInst) % 4 == 0, "copied as 32-bit words");
+  const int* src = reinterpret_cast<const int*>(tab + i);
+  int* d = reinterpret_cast<int*>(&dst);
+  for (int k = threadIdx.x; k < (int)(sizeof(SwInst) / 4); k += blockDim.x) d[k] = __ldg(src + k);
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(NTHREADS, 3) k_sw_apply4_batch(const SwInst* __restrict__ tab,
+                                                             const int* __restrict__ off, int n, int slot, int j,
+                                                             double btol) {
+  __shared__ SwInst I;
+  const int i = inst_of(off, n, blockIdx.x);
+  load_inst(I, tab, i);
+  pdl_wait();
+  const Slot<float> s = I.s[slot];
+  if (s.st->done || s.st->retired) return;
+  sw_apply4_body(I.g, s, I.w[slot], j, I.ld, I.ie, I.sig2, I.ldh, I.ns, btol, (int)blockIdx.x - I.a0, I.na);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s_batch(const SwInst* __restrict__ tab,
+                                                             const int* __restrict__ off, int n, int slot, int j) {
+  __shared__ SwInst I;
+  const int i = inst_of(off, n, blockIdx.x);
+  load_inst(I, tab, i);
+  pdl_wait();
+  const Slot<float> s = I.s[slot];
+  if (s.st->done || s.st->retired) return;
+  sw_pass4s_body(I.g, s, I.w[slot], j, I.ld, I.ie, I.sig2, (int)blockIdx.x - I.s0, I.ns);
+}
+
+// After the last sweep: one block per problem.
+__global__ void __launch_bounds__(NTHREADS) k_sw_last_batch(const SwInst* __restrict__ tab, int slot, int m,
+                                                            double btol) {
+  __shared__ SwInst I;
+  load_inst(I, tab, blockIdx.x);
+  pdl_wait();
+  const Slot<float> s = I.s[slot];
+  if (s.st->done || s.st->retired) return;
+  const SwSlot w = I.w[slot];
+  const double x = block_column_sum(w.part, w.ps, 2 * m, I.ns);
+  if (threadIdx.x == 0) w.co->tot[2 * m] = x;
+  __syncthreads();
+  sw_fin<float>(s, w.co, w.G, m, I.ldh, btol, 1);
+}
+
 }  // namespace
 
 template <typename T>
 constexpr double sw_btol() { return sizeof(T) == 8 ? 1e-12 : 1e-6; }
+
+size_t sweep_smem_bytes() { return SW_SMEM; }
+const void* sweep_batch_kernel() { return (const void*)k_sw_pass4s_batch; }
+
+// Launch with programmatic dependent launch (the bodies wait for their
+// predecessor before touching data and trigger their successor near the end).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+kx_status sweep_arnoldi_batch(kx_ctx* c0, cudaStream_t st, const SwInst* tab, const int* aoff, const int* soff, int n,
+                              int na, int ns, int slot, int m, int64_t* launches) {
+  static SmemOptIn smem{};
+  const kx_status so = smem_opt_in(c0, smem, (const void*)k_sw_pass4s_batch, SW_SMEM);
+  if (so != KX_OK) return so;
+  const double bt = sw_btol<float>();
+  for (int j = 0; j <= m; ++j) {
+    cudaError_t e = cudaSuccess;
+    if (j >= 1) {
+      e = launch_pdl(k_sw_pass4s_batch, ns, SW_SMEM, st, tab, soff, n, slot, j);
+      if (e == cudaSuccess) ++*launches;
+    }
+    if (e == cudaSuccess) {
+      e = j == m ? launch_pdl(k_sw_last_batch, n, 0, st, tab, slot, m, bt)
+                 : launch_pdl(k_sw_apply4_batch, na, 0, st, tab, aoff, n, slot, j, bt);
+      if (e == cudaSuccess) ++*launches;
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      snprintf(c0->err, sizeof(c0->err), "batched Arnoldi launch failed: %s", cudaGetErrorString(e));
+      return KX_ECUDA;
+    }
+  }
+  return KX_OK;
+}
 
 static SwSlot sw_slot(kx_ctx* c, int slot) {
   SwSlot w;

@@ -384,26 +384,26 @@ def wall_keep_mask(grid: Grid) -> np.ndarray:
     return keep.reshape(-1)
 
 
-def uneven_batch(count=48, seed=1711, nmin=32, nmax=96):
-    """Instances for the uneven batch: cubic sizes drawn from U{nmin..nmax},
-    inclusion permittivity from {2.25, 4}, fill from U[0.2, 0.4], four
-    frequencies each in [0.9, 1.1] * OMEGA0."""
+def uneven_batch(count=48, seed=1711, nmin=32, nmax=96, step=1):
+    """Instances for the uneven batch: cubic sizes drawn uniformly from
+    {nmin, nmin + step, ..., nmax}, inclusion permittivity from {2.25, 4},
+    fill from U[0.2, 0.4], four frequencies each in [0.9, 1.1] * OMEGA0."""
     rng = PCG32(seed)
     out = []
     for b in range(count):
-        n = rng.randint(nmin, nmax)
+        n = nmin + step * rng.randint(0, (nmax - nmin) // step)
         e = 2.25 if rng.randint(0, 1) == 0 else 4.0
         f = rng.uniform(0.2, 0.4)
         out.append((n, e, f, seed * 1000 + b))
     return out
 
 
-def config_uneven(count=48, seed=1711, nmin=32, nmax=96, T=400.0, m=64, nfreq=4):
-    """The uneven batch: ``count`` 3D instances with cubic sizes U{nmin..nmax},
-    inclusion permittivity from {2.25, 4}, fill U[0.2, 0.4], each with
-    ``nfreq`` frequencies in [0.9, 1.1] * OMEGA0."""
+def config_uneven(count=48, seed=1711, nmin=32, nmax=96, T=400.0, m=64, nfreq=4, step=1):
+    """The uneven batch: ``count`` 3D instances with cubic sizes drawn from
+    {nmin, nmin + step, ..., nmax}, inclusion permittivity from {2.25, 4},
+    fill U[0.2, 0.4], each with ``nfreq`` frequencies in [0.9, 1.1] * OMEGA0."""
     out = []
-    for (n, e, f, s) in uneven_batch(count, seed, nmin, nmax):
+    for (n, e, f, s) in uneven_batch(count, seed, nmin, nmax, step):
         sc = config_3d(n=n, seed=s, fill=f, T=T, m=m, eps_choices=(e,))
         sc.omegas = OMEGA0 * np.linspace(0.9, 1.1, nfreq)
         sc.name = f"uneven_n{n}_e{e}_f{f:.2f}"
