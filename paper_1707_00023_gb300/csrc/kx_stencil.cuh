@@ -314,6 +314,65 @@ __device__ __forceinline__ void stencil_quad(const Geo& g, const float* __restri
   }
 }
 
+// The same rows on one cell, 32-bit cell indices (the caller ensures
+// ncell < 2^31): out[c] = component c of A v at the cell, bit for bit what
+// stencil_quad gives there (the same operations in the same order).  Few
+// registers, so a flat grid of one cell a thread keeps more warps resident
+// than the quad form (whose sixteen-byte loads need about twice the
+// registers).
+__device__ __forceinline__ void stencil_cell32(const Geo& g, const float* __restrict__ v, const float* __restrict__ ie,
+                                               const float* __restrict__ sig2, int cell, float out[6]) {
+  const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+  const int nc = (int)g.ncell;
+  const int i = cell % nx, r = cell / nx, j = r % ny, k = r / ny;
+  const int ip = i + 1 == nx ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+  const int jp = j + 1 == ny ? 0 : j + 1, jm = j == 0 ? ny - 1 : j - 1;
+  const int kp = k + 1 == nz ? 0 : k + 1, km = k == 0 ? nz - 1 : k - 1;
+  const int cip = cell + (ip - i), cim = cell + (im - i);
+  const int cjp = cell + (jp - j) * nx, cjm = cell + (jm - j) * nx;
+  const int ckp = cell + (kp - k) * nxy, ckm = cell + (km - k) * nxy;
+  const float* __restrict__ vHx = v;
+  const float* __restrict__ vHy = v + (int64_t)nc;
+  const float* __restrict__ vHz = v + 2 * (int64_t)nc;
+  const float* __restrict__ vEx = v + 3 * (int64_t)nc;
+  const float* __restrict__ vEy = v + 4 * (int64_t)nc;
+  const float* __restrict__ vEz = v + 5 * (int64_t)nc;
+  const float hx = is_wall(g, 0, i, j, k) ? 0.f : vHx[cell];
+  const float hy = is_wall(g, 1, i, j, k) ? 0.f : vHy[cell];
+  const float hz = is_wall(g, 2, i, j, k) ? 0.f : vHz[cell];
+  const float ex = is_wall(g, 3, i, j, k) ? 0.f : vEx[cell];
+  const float ey = is_wall(g, 4, i, j, k) ? 0.f : vEy[cell];
+  const float ez = is_wall(g, 5, i, j, k) ? 0.f : vEz[cell];
+  const float ez_jp = is_wall(g, 5, i, jp, k) ? 0.f : vEz[cjp];
+  const float ex_jp = is_wall(g, 3, i, jp, k) ? 0.f : vEx[cjp];
+  const float ey_kp = is_wall(g, 4, i, j, kp) ? 0.f : vEy[ckp];
+  const float ex_kp = is_wall(g, 3, i, j, kp) ? 0.f : vEx[ckp];
+  const float hz_jm = is_wall(g, 2, i, jm, k) ? 0.f : vHz[cjm];
+  const float hx_jm = is_wall(g, 0, i, jm, k) ? 0.f : vHx[cjm];
+  const float hy_km = is_wall(g, 1, i, j, km) ? 0.f : vHy[ckm];
+  const float hx_km = is_wall(g, 0, i, j, km) ? 0.f : vHx[ckm];
+  const float ez_ip = is_wall(g, 5, ip, j, k) ? 0.f : vEz[cip];
+  const float ey_ip = is_wall(g, 4, ip, j, k) ? 0.f : vEy[cip];
+  const float hz_im = is_wall(g, 2, im, j, k) ? 0.f : vHz[cim];
+  const float hy_im = is_wall(g, 1, im, j, k) ? 0.f : vHy[cim];
+  const int li = g.la == 0 ? i : (g.la == 1 ? j : k);
+  float sg[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) sg[c] = sig2[2 * li + g.sighalf[c]];
+  const float cHx = (hz - hz_jm) - (hy - hy_km);
+  const float cHy = (hx - hx_km) - (hz - hz_im);
+  const float cHz = (hy - hy_im) - (hx - hx_jm);
+  float o[6];
+  o[0] = sg[0] * hx + ((ez_jp - ez) - (ey_kp - ey));
+  o[1] = sg[1] * hy + ((ex_kp - ex) - (ez_ip - ez));
+  o[2] = sg[2] * hz + ((ey_ip - ey) - (ex_jp - ex));
+  o[3] = ie[cell] * (sg[3] * ex - cHx);
+  o[4] = ie[nc + cell] * (sg[4] * ey - cHy);
+  o[5] = ie[2 * (int64_t)nc + cell] * (sg[5] * ez - cHz);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) out[c] = is_wall(g, c, i, j, k) ? 0.f : o[c];
+}
+
 // L2 prefetch of the lines stencil_quad reads for a quad (its own six
 // components, the y and z neighbours it uses, the three 1/eps rows): issued
 // one quad (or tile) ahead, it lets a latency-bound loop keep the next
