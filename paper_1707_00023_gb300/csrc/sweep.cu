@@ -697,7 +697,10 @@ __device__ __forceinline__ void sw_pass4s_body(const Geo& g, const Slot<float>& 
   bool act = false, ok = true;
   int64_t c0 = 0, tile = bid;
   int col = 0;
-  for (int64_t e = 0; e < E; ++e) {
+  // Elements are consumed two at a time (two columns of the same tile, one
+  // block barrier and two refills per pair), one at a time at a tile's odd
+  // end; the arithmetic of every column is the same either way.
+  for (int64_t e = 0; e < E;) {
     if (col == 0) {
       // a tile starts: x = A v_{j-1}, y = A^2 v_{j-1} - h_{j-1,j-1} A v_{j-1}
       const int64_t q4 = tile * NTHREADS + threadIdx.x;
@@ -723,45 +726,52 @@ __device__ __forceinline__ void sw_pass4s_body(const Geo& g, const Slot<float>& 
         for (int c = 0; c < 6; ++c) x[c] = xl[c] = y[c] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
-    if (col == j - 1) {
-      // the tile's last column: prefetch the next tile's stencil inputs
+    const int cnt = col + 1 < j ? 2 : 1;   // elements e .. e + cnt - 1: columns col .. col + cnt - 1
+    const bool ends = col + cnt == j;      // the group holds the tile's last column
+    if (ends) {
+      // prefetch the next tile's stencil inputs
       const int64_t qn = (tile + nblk) * NTHREADS + threadIdx.x;
       if (qn < nq) prefetch_quad(g, t, ie, make_quad(g, qn));
     }
-    const int b = (int)(e & (SW_STAGES - 1));
-    if (ok) ok = mbar_wait(&full[b], (unsigned)((e >> 2) & 1));
-    float pa = 0.f, pb = 0.f;
-    if (act) {
-      // an inactive thread reads no buffer (the tile's tail is not copied)
-      const float* sb = ring + b * SW_STAGE_FLOATS + 4 * threadIdx.x;
-      float4 vv[6];
+#pragma unroll 1
+    for (int q = 0; q < cnt; ++q) {
+      const int64_t ee = e + q;
+      const int cq = col + q;
+      const int b = (int)(ee & (SW_STAGES - 1));
+      if (ok) ok = mbar_wait(&full[b], (unsigned)((ee >> 2) & 1));
+      float pa = 0.f, pb = 0.f;
+      if (act) {
+        // an inactive thread reads no buffer (the tile's tail is not copied)
+        const float* sb = ring + b * SW_STAGE_FLOATS + 4 * threadIdx.x;
+        float4 vv[6];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) vv[c] = *reinterpret_cast<const float4*>(sb + c * SW_TILE);
-      // two independent accumulator chains per dot (the quad's two halves)
-      float2 sa = make_float2(0.f, 0.f), sa2 = sa, sx = sa, sx2 = sa;
+        for (int c = 0; c < 6; ++c) vv[c] = *reinterpret_cast<const float4*>(sb + c * SW_TILE);
+        // two independent accumulator chains per dot (the quad's two halves)
+        float2 sa = make_float2(0.f, 0.f), sa2 = sa, sx = sa, sx2 = sa;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        sa = __ffma2_rn(lo2(vv[c]), lo2(y[c]), sa);
-        sa2 = __ffma2_rn(hi2(vv[c]), hi2(y[c]), sa2);
-        sx = __ffma2_rn(lo2(vv[c]), lo2(x[c]), sx);
-        sx2 = __ffma2_rn(hi2(vv[c]), hi2(x[c]), sx2);
+        for (int c = 0; c < 6; ++c) {
+          sa = __ffma2_rn(lo2(vv[c]), lo2(y[c]), sa);
+          sa2 = __ffma2_rn(hi2(vv[c]), hi2(y[c]), sa2);
+          sx = __ffma2_rn(lo2(vv[c]), lo2(x[c]), sx);
+          sx2 = __ffma2_rn(hi2(vv[c]), hi2(x[c]), sx2);
+        }
+        pa = (sa.x + sa2.x) + (sa.y + sa2.y);
+        pb = (sx.x + sx2.x) + (sx.y + sx2.y);
+        const float2 na = make_float2(-ch[cq], -ch[cq]), nb = make_float2(-cc[cq], -cc[cq]);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          float2 h0 = lo2(x[c]), h1 = hi2(x[c]), l0 = lo2(xl[c]), l1 = hi2(xl[c]);
+          sub_fma2(h0, l0, na, lo2(vv[c]));
+          sub_fma2(h1, l1, na, hi2(vv[c]));
+          x[c] = join2(h0, h1);
+          xl[c] = join2(l0, l1);
+          y[c] = join2(__ffma2_rn(nb, lo2(vv[c]), lo2(y[c])), __ffma2_rn(nb, hi2(vv[c]), hi2(y[c])));
+        }
       }
-      pa = (sa.x + sa2.x) + (sa.y + sa2.y);
-      pb = (sx.x + sx2.x) + (sx.y + sx2.y);
-      const float2 na = make_float2(-ch[col], -ch[col]), nb = make_float2(-cc[col], -cc[col]);
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        float2 h0 = lo2(x[c]), h1 = hi2(x[c]), l0 = lo2(xl[c]), l1 = hi2(xl[c]);
-        sub_fma2(h0, l0, na, lo2(vv[c]));
-        sub_fma2(h1, l1, na, hi2(vv[c]));
-        x[c] = join2(h0, h1);
-        xl[c] = join2(l0, l1);
-        y[c] = join2(__ffma2_rn(nb, lo2(vv[c]), lo2(y[c])), __ffma2_rn(nb, hi2(vv[c]), hi2(y[c])));
-      }
+      const float r = warp_sum2(pa, pb, lane);
+      if ((lane & 15) == 0) acc[warp][(lane >> 4) * j + cq] += (double)r;
     }
-    const float r = warp_sum2(pa, pb, lane);
-    if ((lane & 15) == 0) acc[warp][(lane >> 4) * j + col] += (double)r;
-    if (col == j - 1) {
+    if (ends) {
       // the tile ends: store V_j = x (hi + lo rounded once), accumulate x.x, x.y, y.y
       float xx = 0.f, xy = 0.f, yy = 0.f;
       if (act) {
@@ -783,7 +793,8 @@ __device__ __forceinline__ void sw_pass4s_body(const Geo& g, const Slot<float>& 
         acc[warp][2 * j + 2] += (double)yy;
       }
     }
-    // every thread is done with buffer b: refill it with element e + SW_STAGES
+    // every thread is done with the group's buffers: refill them with
+    // elements e + SW_STAGES ..
     if (!__syncthreads_and(ok)) {
       if (threadIdx.x == 0) {
         s.st->status = KX_ETIMEOUT;
@@ -793,12 +804,17 @@ __device__ __forceinline__ void sw_pass4s_body(const Geo& g, const Slot<float>& 
       }
       return;
     }
-    if (threadIdx.x == 0 && e + SW_STAGES < E) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      sw_issue(s, ld, nc, cur.tile, cur.col, b, ring, full);
-      cur.next(j);
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < cnt; ++q) {
+        if (e + q + SW_STAGES >= E) break;
+        if (q == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        sw_issue(s, ld, nc, cur.tile, cur.col, (int)((e + q) & (SW_STAGES - 1)), ring, full);
+        cur.next(j);
+      }
     }
-    if (++col == j) {
+    e += cnt;
+    col += cnt;
+    if (col == j) {
       col = 0;
       tile += nblk;
     }
