@@ -377,6 +377,52 @@ def run_uneven(args, w):
     launches0 = launch_count()
     dev_ms, wall, clk = timed_steps(args, dist, step, main_stream)
     launches = launch_count() - launches0
+    roofline = e2e = cpu = None
+    if batch is not None:
+        # end to end: every instance's source from pinned host memory, the
+        # intensities back to the host (the call returns them there)
+        hosts = [torch.tensor(sc.g, dtype=dt).pin_memory() for sc in scs]
+        torch.cuda.synchronize()
+        e0 = time.perf_counter()
+        for _ in range(args.steps):
+            gd = [h.to("cuda", non_blocking=True) for h in hosts]
+            torch.cuda.synchronize()
+            batch.response(gd, oms, w["T"], rtol=w["rtol"], planes=planes)
+        e_wall = barrier_max(dist, time.perf_counter() - e0)
+        e2e = {"value": len(scs) * w["nfreq"] * args.steps * world / e_wall, "unit": "responses/s",
+               "h2d_bytes_per_step": int(sum(h.numel() * h.element_size() for h in hosts)),
+               "d2h_bytes_per_step": int(3 * 8 * len(scs) * w["nfreq"])}
+        # roofline of the batched sweep (an untimed pass with its launches timed by events)
+        i0 = batch.info()
+        batch.set_timing(True)
+        step()
+        batch.set_timing(False)
+        i1 = batch.info()
+        ms = i1["sweep_ms"] - i0["sweep_ms"]
+        nl = i1["sweep_timed_launches"] - i0["sweep_timed_launches"]
+        by = i1["sweep_bytes"] - i0["sweep_bytes"]
+        peak, peak_kind = peaks()
+        if ms > 0 and nl > 0:
+            ach = by / (ms / 1000.0) / 1e9
+            roofline = {"bound": "hbm", "kernel": "k_sw_pass4s_batch", "achieved": round(ach, 1), "peak": peak,
+                        "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
+                        "algorithmic_bytes_per_launch": round(by / nl), "peak_source": peak_kind,
+                        "launches": nl, "avg_launch_us": round(1000 * ms / nl, 2)}
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            # the oracle on 3 seeded instances: per-response seconds from its pieces, averaged
+            rng = np.random.default_rng(1707 + 4)
+            picks = sorted(int(i) for i in rng.choice(len(scs), size=3, replace=False))
+            secs, parts = [], []
+            for i in picks:
+                orc = OraclePieces(w, scs[i])
+                el = sum(orc.step() for _ in range(2))
+                secs.append(orc.pieces * el / 2)
+                parts.append(f"instance {i} ({scs[i].grid.n[0]}^3): {el / 2:.2f} s a piece x {orc.pieces} pieces")
+            cpu = {"value": 1.0 / float(np.mean(secs)), "unit": "responses/s", "cores": 1, "kind": "oracle",
+                   "sample": "oracle exact response (augmented route, scipy expm_multiply, FP64) of one frequency "
+                             "on each of 3 seeded instances, 2 equal pieces of [0, T] each, per-response time = "
+                             "pieces x piece time, averaged over the instances: " + "; ".join(parts),
+                   **cpu_info()}
     # device events on the current stream do not order the instance streams;
     # the wall clock around the synchronised call is the job time here
     job_s = barrier_max(dist, wall)
@@ -394,8 +440,8 @@ def run_uneven(args, w):
                            "driver": "batched launches" if batch is not None else f"{w['threads']} host threads",
                            "timing": "wall clock around the synchronised multi-problem call",
                            "media_generation_s": round(t_gen, 1)},
-                "gpu_launches": launches, "clocks": clk, "roofline": None, "cpu_baseline": None,
-                "e2e": None}
+                "gpu_launches": launches, "clocks": clk, "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": e2e}
         if batch is not None:
             line["autotune"] = tune
         print(json.dumps(line), flush=True)

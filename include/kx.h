@@ -361,10 +361,21 @@ typedef struct {
   int from_cache;               /* 1: the choice came from an earlier batch    */
   double tune_ms;               /* time the timing runs took (0 if cached)     */
   int64_t batched_launches;     /* batched Arnoldi launches so far             */
+  double sweep_ms;              /* summed event time of the timed batched sweep
+                                   launches (kx_batch_set_timing)              */
+  double sweep_bytes;           /* their algorithmic bytes: per problem still
+                                   running (j+2) n s + 3 ncell s at step j     */
+  int64_t sweep_timed_launches;
 } kx_batch_info;
 kx_status kx_batch_create(kx_ctx* const* ctxs, int nctx, void* cuda_stream, kx_batch** out);
 kx_status kx_batch_destroy(kx_batch* batch);
 kx_status kx_batch_get_info(const kx_batch* batch, kx_batch_info* out);
+/* Per-launch timing of the batched sweep launches (a measurement aid, off by
+ * default): with it on, each batched sweep launch is bracketed by CUDA events
+ * on the batch's stream, and the totals appear in kx_batch_info after each
+ * batched call.  The events break the programmatic overlap between
+ * neighbouring launches; leave it off in timed runs. */
+kx_status kx_batch_set_timing(kx_batch* batch, int on);
 const char* kx_batch_last_error(const kx_batch* batch);
 
 /* Responses of every problem of a batch by restart in Krylov dimension (as

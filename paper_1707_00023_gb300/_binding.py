@@ -30,7 +30,7 @@ EXPORTS = ["krylov_expm_create", "krylov_expm_create_mat", "krylov_expm_destroy"
            "kx_kernel_times", "kx_last_error", "kx_arnoldi_noalloc", "kx_noalloc_last_error",
            "adjoint_response_grad", "kx_set_permittivity", "response_at_freqs_multi", "kx_stream",
            "response_restart_dim", "kx_wait_selftest", "kx_batch_create", "kx_batch_destroy",
-           "kx_batch_get_info", "kx_batch_last_error", "response_restart_dim_batch"]
+           "kx_batch_get_info", "kx_batch_last_error", "response_restart_dim_batch", "kx_batch_set_timing"]
 KCLASSES = ["pass_a", "pass_b", "restart", "projected", "zupdate", "apply", "cascade", "sweep", "swapply"]
 # Arnoldi forms (kx_desc.arnoldi_form)
 ARNOLDI_FORMS = {"default": 0, "twopass": 1, "sweep": 2}
@@ -59,7 +59,8 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("problems", ctypes.c_int), ("sweep_tiles_per_block", ctypes.c_int),
                 ("apply_rounds_per_thread", ctypes.c_int), ("sweep_blocks", ctypes.c_int),
                 ("apply_blocks", ctypes.c_int), ("from_cache", ctypes.c_int), ("tune_ms", ctypes.c_double),
-                ("batched_launches", ctypes.c_int64)]
+                ("batched_launches", ctypes.c_int64), ("sweep_ms", ctypes.c_double), ("sweep_bytes", ctypes.c_double),
+                ("sweep_timed_launches", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):
@@ -118,6 +119,7 @@ def load_library(path: Optional[str] = None):
     lib.kx_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
     lib.kx_batch_destroy.argtypes = [vp]
     lib.kx_batch_get_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
+    lib.kx_batch_set_timing.argtypes = [vp, ctypes.c_int]
     lib.kx_batch_last_error.argtypes = [vp]
     lib.kx_batch_last_error.restype = ctypes.c_char_p
     lib.response_restart_dim_batch.argtypes = [vp, ctypes.POINTER(vp), dp, ctypes.c_int, ctypes.c_double,
@@ -447,6 +449,9 @@ class Batch:
         if st != KX_OK:
             raise KxError(st, self.lib.kx_batch_last_error(None).decode())
         self.h = h
+
+    def set_timing(self, on: bool):
+        self.lib.kx_batch_set_timing(self.h, int(bool(on)))
 
     def info(self):
         i = BatchInfo()

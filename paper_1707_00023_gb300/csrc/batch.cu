@@ -47,6 +47,12 @@ struct kx_batch {
   cudaEvent_t ev_arn = nullptr;
   int* h_pin = nullptr;          // pinned host words: per problem MAXF states + a status; one word = 1
   int64_t launches = 0;
+  // per-launch event timing of the batched sweep launches (kx_batch_set_timing)
+  int timing = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sweep_events;
+  std::vector<double> sweep_bytes;   // algorithmic bytes of each timed launch
+  double sweep_ms = 0.0, sweep_bytes_sum = 0.0;
+  int64_t sweep_timed = 0;
   char err[512] = {0};
 };
 
@@ -155,12 +161,47 @@ kx_status set_grids(kx_batch* b, int tpb, int rpt) {
   return KX_OK;
 }
 
-kx_status arnoldi_all(kx_batch* b, int slot) {
+// Algorithmic bytes of the batched sweep S_j over the problems still
+// running: (j + 2) n_i s + 3 ncell_i s each (basis columns, t, the new
+// column, 1/eps), the single-problem count summed.
+double sweep_bytes_of(const kx_batch* b, int j, const std::vector<char>* active) {
+  double sum = 0.0;
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    if (active && !(*active)[i]) continue;
+    const kx_ctx* c = b->ctx[i];
+    sum += (j + 2.0) * (double)c->n * c->esize + 3.0 * (double)c->geo.ncell * c->esize;
+  }
+  return sum;
+}
+
+kx_status arnoldi_all(kx_batch* b, int slot, const std::vector<char>* active = nullptr) {
   const int n = (int)b->ctx.size();
+  const size_t before = b->sweep_events.size();
   const kx_status st = sweep_arnoldi_batch(b->ctx[0], b->stream, b->d_tab, b->d_off, b->d_off + n + 1, n, b->na,
-                                           b->ns, slot, b->ctx[0]->m, &b->launches);
+                                           b->ns, slot, b->ctx[0]->m, &b->launches,
+                                           b->timing ? &b->sweep_events : nullptr);
+  if (b->timing)
+    for (size_t k = before; k < b->sweep_events.size(); ++k)
+      b->sweep_bytes.push_back(sweep_bytes_of(b, (int)(k - before) + 1, active));
   if (st != KX_OK) return bfail(b, st, b->ctx[0]->err);
   return KX_OK;
+}
+
+// Fold the recorded sweep events into the totals (the stream is synchronised).
+void collect_timing(kx_batch* b) {
+  for (size_t k = 0; k < b->sweep_events.size(); ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, b->sweep_events[k].first, b->sweep_events[k].second) == cudaSuccess) {
+      b->sweep_ms += ms;
+      b->sweep_bytes_sum += b->sweep_bytes[k];
+      b->sweep_timed += 1;
+    }
+    cudaEventDestroy(b->sweep_events[k].first);
+    cudaEventDestroy(b->sweep_events[k].second);
+  }
+  cudaGetLastError();
+  b->sweep_events.clear();
+  b->sweep_bytes.clear();
 }
 
 // A fixed pseudo-random start vector (the autotuner's timing input).
@@ -335,9 +376,20 @@ kx_status kx_batch_create(kx_ctx* const* ctxs, int nctx, void* cuda_stream, kx_b
   return KX_OK;
 }
 
+kx_status kx_batch_set_timing(kx_batch* b, int on) {
+  if (!b) return KX_EINVAL;
+  b->timing = on ? 1 : 0;
+  if (!on) {
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    collect_timing(b);
+  }
+  return KX_OK;
+}
+
 kx_status kx_batch_destroy(kx_batch* b) {
   if (!b) return KX_OK;
   if (b->stream) cudaStreamSynchronize(b->stream);
+  collect_timing(b);
   if (b->d_tab) cudaFree(b->d_tab);
   if (b->d_off) cudaFree(b->d_off);
   if (b->h_pin) cudaFreeHost(b->h_pin);
@@ -357,6 +409,9 @@ kx_status kx_batch_get_info(const kx_batch* b, kx_batch_info* out) {
   out->from_cache = b->from_cache;
   out->tune_ms = b->tune_ms;
   out->batched_launches = b->launches;
+  out->sweep_ms = b->sweep_ms;
+  out->sweep_bytes = b->sweep_bytes_sum;
+  out->sweep_timed_launches = b->sweep_timed;
   return KX_OK;
 }
 
@@ -421,7 +476,7 @@ kx_status response_restart_dim_batch(kx_batch* b, const void* const* d_g, const 
       for (int s2 = 0; s2 < 2; ++s2)
         KB_CUDA(b, cudaMemcpyAsync(&b->ctx[i]->d_state[s2].retired, one, sizeof(int), cudaMemcpyHostToDevice, S),
                 "retire");
-  KB_OK(arnoldi_all(b, 0));
+  KB_OK(arnoldi_all(b, 0, &active));
   KB_OK(read_slot_states(b, 0));
   // sample grid of each problem from ||H_m||_1 of its first restart
   std::vector<int> Nt(n, 0), kmax(n, 0), rcount((size_t)n * nfreq, 0);
@@ -491,7 +546,7 @@ kx_status response_restart_dim_batch(kx_batch* b, const void* const* d_g, const 
         KB_TRY(b, c, launch_rst_nextvec(c, S, sl, nx));
         KB_TRY(b, c, launch_norm_init(c, nx, 1));
       }
-      KB_OK(arnoldi_all(b, nx));
+      KB_OK(arnoldi_all(b, nx, &active));
       KB_CUDA(b, cudaEventRecord(b->ev_arn, S), "event record");
     }
     // restart k's stopping tests (Fig. alg:rst step 2(c))
@@ -543,6 +598,7 @@ kx_status response_restart_dim_batch(kx_batch* b, const void* const* d_g, const 
             "residual read");
   }
   KB_CUDA(b, cudaStreamSynchronize(S), "stream synchronise");
+  if (b->timing) collect_timing(b);
   for (int i = 0; i < n; ++i) {
     kx_ctx* c = b->ctx[i];
     for (int f = 0; f < nfreq; ++f) {

@@ -308,7 +308,8 @@ kx_status sweep_arnoldi(kx_ctx* c, int slot, int m);
 // launch per Arnoldi phase; tab/aoff/soff device copies of the instance
 // table and of the block offsets (n + 1 entries each), na/ns the launch totals
 kx_status sweep_arnoldi_batch(kx_ctx* c0, cudaStream_t st, const SwInst* tab, const int* aoff, const int* soff, int n,
-                              int na, int ns, int slot, int m, int64_t* launches);
+                              int na, int ns, int slot, int m, int64_t* launches,
+                              std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* sweep_events);
 size_t sweep_smem_bytes();
 const void* sweep_batch_kernel();
 // the bounded mbarrier wait of the sweep on a barrier nothing completes

@@ -537,15 +537,6 @@ __device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x,
 __device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
 __device__ __forceinline__ float4 join2(const float2& a, const float2& b) { return make_float4(a.x, a.y, b.x, b.y); }
 
-// The compensated update of kx_eft.cuh (sub_fma), two lanes at a time in
-// packed FP32x2 operations: hi + lo <- hi + lo + nch v.
-__device__ __forceinline__ void sub_fma2(float2& hi, float2& lo, float2 nch, float2 v) {
-  const float2 m1 = make_float2(-1.f, -1.f);
-  const float2 s = __ffma2_rn(nch, v, hi);    // fl(hi + nch v)
-  const float2 d = __ffma2_rn(s, m1, hi);     // hi - s, exact when s is within a factor 2 of hi
-  lo = __fadd2_rn(lo, __ffma2_rn(nch, v, d)); // + the rounding error of s
-  hi = s;
-}
 
 // Warp sums of two values in a fixed order: lane l ends with the sum of
 // value (l >> 4) & 1, so lanes 0 and 16 hold the sums of v0 and v1.
@@ -936,7 +927,8 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, size_t smem, cud
 }
 
 kx_status sweep_arnoldi_batch(kx_ctx* c0, cudaStream_t st, const SwInst* tab, const int* aoff, const int* soff, int n,
-                              int na, int ns, int slot, int m, int64_t* launches) {
+                              int na, int ns, int slot, int m, int64_t* launches,
+                              std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* sweep_events) {
   static SmemOptIn smem{};
   const kx_status so = smem_opt_in(c0, smem, (const void*)k_sw_pass4s_batch, SW_SMEM);
   if (so != KX_OK) return so;
@@ -944,8 +936,20 @@ kx_status sweep_arnoldi_batch(kx_ctx* c0, cudaStream_t st, const SwInst* tab, co
   for (int j = 0; j <= m; ++j) {
     cudaError_t e = cudaSuccess;
     if (j >= 1) {
+      // optional event pair around the sweep launch (a measurement aid; the
+      // events break the programmatic overlap with the neighbouring launches)
+      cudaEvent_t ea = nullptr, eb = nullptr;
+      if (sweep_events) {
+        cudaEventCreate(&ea);
+        cudaEventCreate(&eb);
+        cudaEventRecord(ea, st);
+      }
       e = launch_pdl(k_sw_pass4s_batch, ns, SW_SMEM, st, tab, soff, n, slot, j);
       if (e == cudaSuccess) ++*launches;
+      if (sweep_events) {
+        cudaEventRecord(eb, st);
+        sweep_events->push_back({ea, eb});
+      }
     }
     if (e == cudaSuccess) {
       e = j == m ? launch_pdl(k_sw_last_batch, n, 0, st, tab, slot, m, bt)

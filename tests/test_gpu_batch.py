@@ -52,9 +52,14 @@ def test_batch_matches_single_problems_and_oracle():
             assert abs(inten[i, f] - alone["intensity"][f]) < 2e-6 * alone["intensity"][f]
             want = yee.intensity(sc.grid, exact.y_plain(A, sc.g, sc.omegas[f], T), sc.plane)
             assert abs(inten[i, f] - want) < 2e-6 * want
-    # the same call again gives the same bits (fixed block split and reduction order)
+    # the same call again gives the same bits (fixed block split and reduction order),
+    # also with the batched sweep launches timed by events
+    b.set_timing(True)
     again, _, _ = b.response(gs, oms, T, rtol=1e-7, planes=planes)
+    b.set_timing(False)
     np.testing.assert_array_equal(again, inten)
+    ti = b.info()
+    assert ti["sweep_timed_launches"] > 0 and ti["sweep_ms"] > 0.0 and ti["sweep_bytes"] > 0.0
     b.close()
     # a second batch of the same size class takes the tuned split from the cache
     b2 = Batch(ctxs)

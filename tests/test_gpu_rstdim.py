@@ -321,3 +321,23 @@ def test_full_size_3d128_T400_default_against_time_restarted_fp64():
     for k, f in enumerate((0, 31)):
         assert rel(a["E_plane"][f].double().cpu().numpy(), b["E_plane"][k].cpu().numpy()) < 1e-6
         assert rel(ya[k], b["Y"][k].cpu().numpy()) < 1e-6
+
+
+def test_default_configuration_128cubed_against_the_oracle_at_T20():
+    """The default benchmark configuration (128^3 benchmark medium, m = 64,
+    32 frequencies, FP32, the single sweep with the compensated update)
+    against the FP64 oracle itself on the full grid, at a final time the
+    oracle finishes in about a minute per frequency (T = 20; the oracle's
+    augmented route in ten pieces): first and last frequency within 1e-6."""
+    sc = S.config_3d(n=128, seed=1710, fill=0.3, T=400.0, m=64)
+    oms = S.freq_list(32)
+    ctx = Context(sc.grid, sc.eps_cell, precision="fp32", krylov_dim=64, max_freqs=32, batch=2, rst_samples=4096)
+    out = ctx.response_restart_dim(dev(sc.g, "fp32"), oms, 20.0, rtol=1e-7, plane=sc.plane, want_full=True)
+    ctx.close()
+    ya = out["Y"][[0, 31]].double().cpu().numpy()
+    del out
+    A = yee.Operator(sc.grid, sc.eps_cell).matrix()
+    eta = float(np.abs(sc.g).sum())
+    for k, f in enumerate((0, 31)):
+        want = exact.y_plain(A, sc.g, float(oms[f]), 20.0, eta=eta, pieces=10)
+        assert rel(ya[k], want) < 1e-6
