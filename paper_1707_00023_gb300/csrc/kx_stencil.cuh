@@ -314,63 +314,190 @@ __device__ __forceinline__ void stencil_quad(const Geo& g, const float* __restri
   }
 }
 
-// The same rows on one cell, 32-bit cell indices (the caller ensures
-// ncell < 2^31): out[c] = component c of A v at the cell, bit for bit what
-// stencil_quad gives there (the same operations in the same order).  Few
-// registers, so a flat grid of one cell a thread keeps more warps resident
-// than the quad form (whose sixteen-byte loads need about twice the
-// registers).
-__device__ __forceinline__ void stencil_cell32(const Geo& g, const float* __restrict__ v, const float* __restrict__ ie,
-                                               const float* __restrict__ sig2, int cell, float out[6]) {
+// Wall bits of the six components along one axis: bit c set when index 0
+// along axis a is a wall node of component c.
+__device__ __forceinline__ unsigned wall_bits(const Geo& g, int a) {
+  unsigned m = 0u;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) m |= ((g.maskbits[c] >> a) & 1u) << c;
+  return m;
+}
+
+// Load of component c at offset idx, zero where bit c of the wall mask w is set.
+__device__ __forceinline__ float ldw(const float* __restrict__ p, int idx, unsigned w, int c) {
+  return (w >> c) & 1u ? 0.f : p[idx];
+}
+
+// t = A v, 3D FP32 lossy-layer model, for the cells of grid column col =
+// i + nx j on planes k0 .. k1-1 (0 <= k0 < k1 <= nz): the rows of
+// stencil_quad with the same operations in the same order (the same bits
+// on every cell), the index and wall work done once per column and, marching
+// up in z, E_x, E_y of plane k+1 and H_x, H_y of plane k kept in registers,
+// where the next plane reads them as its own and its k-1 values (14 field
+// loads a cell instead of 18).  32-bit cell offsets: ncell < 2^31.
+__device__ __forceinline__ void stencil_column32(const Geo& g, const float* __restrict__ v,
+                                                 const float* __restrict__ ie, const float* __restrict__ sig2,
+                                                 float* __restrict__ t, int col, int k0, int k1) {
   const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
   const int nc = (int)g.ncell;
-  const int i = cell % nx, r = cell / nx, j = r % ny, k = r / ny;
+  const int i = col % nx, j = col / nx;
   const int ip = i + 1 == nx ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
   const int jp = j + 1 == ny ? 0 : j + 1, jm = j == 0 ? ny - 1 : j - 1;
-  const int kp = k + 1 == nz ? 0 : k + 1, km = k == 0 ? nz - 1 : k - 1;
-  const int cip = cell + (ip - i), cim = cell + (im - i);
-  const int cjp = cell + (jp - j) * nx, cjm = cell + (jm - j) * nx;
-  const int ckp = cell + (kp - k) * nxy, ckm = cell + (km - k) * nxy;
+  const int dip = ip - i, dim = im - i, djp = (jp - j) * nx, djm = (jm - j) * nx;
+  const unsigned xm = wall_bits(g, 0), ym = wall_bits(g, 1), zm = wall_bits(g, 2);
+  // wall masks of the columns read: (i, j), (ip, j), (im, j), (i, jp), (i, jm)
+  const unsigned wc = (i == 0 ? xm : 0u) | (j == 0 ? ym : 0u);
+  const unsigned wip = (ip == 0 ? xm : 0u) | (j == 0 ? ym : 0u);
+  const unsigned wim = (im == 0 ? xm : 0u) | (j == 0 ? ym : 0u);
+  const unsigned wjp = (i == 0 ? xm : 0u) | (jp == 0 ? ym : 0u);
+  const unsigned wjm = (i == 0 ? xm : 0u) | (jm == 0 ? ym : 0u);
   const float* __restrict__ vHx = v;
-  const float* __restrict__ vHy = v + (int64_t)nc;
+  const float* __restrict__ vHy = v + nc;
   const float* __restrict__ vHz = v + 2 * (int64_t)nc;
   const float* __restrict__ vEx = v + 3 * (int64_t)nc;
   const float* __restrict__ vEy = v + 4 * (int64_t)nc;
   const float* __restrict__ vEz = v + 5 * (int64_t)nc;
-  const float hx = is_wall(g, 0, i, j, k) ? 0.f : vHx[cell];
-  const float hy = is_wall(g, 1, i, j, k) ? 0.f : vHy[cell];
-  const float hz = is_wall(g, 2, i, j, k) ? 0.f : vHz[cell];
-  const float ex = is_wall(g, 3, i, j, k) ? 0.f : vEx[cell];
-  const float ey = is_wall(g, 4, i, j, k) ? 0.f : vEy[cell];
-  const float ez = is_wall(g, 5, i, j, k) ? 0.f : vEz[cell];
-  const float ez_jp = is_wall(g, 5, i, jp, k) ? 0.f : vEz[cjp];
-  const float ex_jp = is_wall(g, 3, i, jp, k) ? 0.f : vEx[cjp];
-  const float ey_kp = is_wall(g, 4, i, j, kp) ? 0.f : vEy[ckp];
-  const float ex_kp = is_wall(g, 3, i, j, kp) ? 0.f : vEx[ckp];
-  const float hz_jm = is_wall(g, 2, i, jm, k) ? 0.f : vHz[cjm];
-  const float hx_jm = is_wall(g, 0, i, jm, k) ? 0.f : vHx[cjm];
-  const float hy_km = is_wall(g, 1, i, j, km) ? 0.f : vHy[ckm];
-  const float hx_km = is_wall(g, 0, i, j, km) ? 0.f : vHx[ckm];
-  const float ez_ip = is_wall(g, 5, ip, j, k) ? 0.f : vEz[cip];
-  const float ey_ip = is_wall(g, 4, ip, j, k) ? 0.f : vEy[cip];
-  const float hz_im = is_wall(g, 2, im, j, k) ? 0.f : vHz[cim];
-  const float hy_im = is_wall(g, 1, im, j, k) ? 0.f : vHy[cim];
-  const int li = g.la == 0 ? i : (g.la == 1 ? j : k);
-  float sg[6];
+  const int km0 = k0 == 0 ? nz - 1 : k0 - 1;
+  unsigned zk = k0 == 0 ? zm : 0u;
+  int cell = col + k0 * nxy;
+  const int ckm0 = col + km0 * nxy;
+  const unsigned wkm0 = wc | (km0 == 0 ? zm : 0u);
+  float hx_km = ldw(vHx, ckm0, wkm0, 0), hy_km = ldw(vHy, ckm0, wkm0, 1);
+  float ex = ldw(vEx, cell, wc | zk, 3), ey = ldw(vEy, cell, wc | zk, 4);
+  for (int k = k0; k < k1; ++k, cell += nxy) {
+    const int kp = k + 1 == nz ? 0 : k + 1;
+    const unsigned zkp = kp == 0 ? zm : 0u;
+    const int ckp = col + kp * nxy;
+    const unsigned mk = wc | zk, mkp = wc | zkp;
+    const float hx = ldw(vHx, cell, mk, 0), hy = ldw(vHy, cell, mk, 1);
+    const float hz = ldw(vHz, cell, mk, 2), ez = ldw(vEz, cell, mk, 5);
+    const float ex_kp = ldw(vEx, ckp, mkp, 3), ey_kp = ldw(vEy, ckp, mkp, 4);
+    const float ez_jp = ldw(vEz, cell + djp, wjp | zk, 5), ex_jp = ldw(vEx, cell + djp, wjp | zk, 3);
+    const float hz_jm = ldw(vHz, cell + djm, wjm | zk, 2), hx_jm = ldw(vHx, cell + djm, wjm | zk, 0);
+    const float ez_ip = ldw(vEz, cell + dip, wip | zk, 5), ey_ip = ldw(vEy, cell + dip, wip | zk, 4);
+    const float hz_im = ldw(vHz, cell + dim, wim | zk, 2), hy_im = ldw(vHy, cell + dim, wim | zk, 1);
+    const int li = g.la == 0 ? i : (g.la == 1 ? j : k);
+    float sg[6];
 #pragma unroll
-  for (int c = 0; c < 6; ++c) sg[c] = sig2[2 * li + g.sighalf[c]];
-  const float cHx = (hz - hz_jm) - (hy - hy_km);
-  const float cHy = (hx - hx_km) - (hz - hz_im);
-  const float cHz = (hy - hy_im) - (hx - hx_jm);
-  float o[6];
-  o[0] = sg[0] * hx + ((ez_jp - ez) - (ey_kp - ey));
-  o[1] = sg[1] * hy + ((ex_kp - ex) - (ez_ip - ez));
-  o[2] = sg[2] * hz + ((ey_ip - ey) - (ex_jp - ex));
-  o[3] = ie[cell] * (sg[3] * ex - cHx);
-  o[4] = ie[nc + cell] * (sg[4] * ey - cHy);
-  o[5] = ie[2 * (int64_t)nc + cell] * (sg[5] * ez - cHz);
+    for (int c = 0; c < 6; ++c) sg[c] = sig2[2 * li + g.sighalf[c]];
+    const float cHx = (hz - hz_jm) - (hy - hy_km);
+    const float cHy = (hx - hx_km) - (hz - hz_im);
+    const float cHz = (hy - hy_im) - (hx - hx_jm);
+    float o[6];
+    o[0] = sg[0] * hx + ((ez_jp - ez) - (ey_kp - ey));
+    o[1] = sg[1] * hy + ((ex_kp - ex) - (ez_ip - ez));
+    o[2] = sg[2] * hz + ((ey_ip - ey) - (ex_jp - ex));
+    o[3] = ie[cell] * (sg[3] * ex - cHx);
+    o[4] = ie[(int64_t)nc + cell] * (sg[4] * ey - cHy);
+    o[5] = ie[2 * (int64_t)nc + cell] * (sg[5] * ez - cHz);
 #pragma unroll
-  for (int c = 0; c < 6; ++c) out[c] = is_wall(g, c, i, j, k) ? 0.f : o[c];
+    for (int c = 0; c < 6; ++c) t[c * (int64_t)nc + cell] = (mk >> c) & 1u ? 0.f : o[c];
+    hx_km = hx;
+    hy_km = hy;
+    ex = ex_kp;
+    ey = ey_kp;
+    zk = zkp;
+  }
+}
+
+// Sixteen-byte load of four x-cells of component c at offset idx (a
+// multiple of 4), zero where the wall mask says so: w0 for the first cell,
+// w1 for the other three (only index 0 along x can be a wall).
+__device__ __forceinline__ float4 ldw4(const float* __restrict__ p, int idx, unsigned w0, unsigned w1, int c) {
+  float4 r = *reinterpret_cast<const float4*>(p + idx);
+  if ((w0 >> c) & 1u) r.x = 0.f;
+  if ((w1 >> c) & 1u) {
+    r.y = 0.f;
+    r.z = 0.f;
+    r.w = 0.f;
+  }
+  return r;
+}
+
+// The column march of stencil_column32 on a quad of x-cells (nx % 4 == 0):
+// quad column q = i0/4 + (nx/4) j, planes k0 .. k1-1; sixteen-byte loads
+// and stores, the x neighbours outside the quad by one scalar load each
+// side, the arithmetic of stencil_quad on every cell (the same bits).
+__device__ __forceinline__ void stencil_column_quad(const Geo& g, const float* __restrict__ v,
+                                                    const float* __restrict__ ie, const float* __restrict__ sig2,
+                                                    float* __restrict__ t, int q, int k0, int k1) {
+  const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny, nqx = nx >> 2;
+  const int nc = (int)g.ncell;
+  const int j = q / nqx, i0 = (q - j * nqx) << 2;
+  const int col = i0 + j * nx;
+  const int jp = j + 1 == ny ? 0 : j + 1, jm = j == 0 ? ny - 1 : j - 1;
+  const int ixp = i0 + 4 == nx ? 0 : i0 + 4, ixm = i0 == 0 ? nx - 1 : i0 - 1;
+  const int dxp = ixp - i0, dxm = ixm - i0, djp = (jp - j) * nx, djm = (jm - j) * nx;
+  const unsigned xm = wall_bits(g, 0), ym = wall_bits(g, 1), zm = wall_bits(g, 2);
+  const unsigned wy = j == 0 ? ym : 0u, wyp = jp == 0 ? ym : 0u, wym = jm == 0 ? ym : 0u;
+  const unsigned wx0 = i0 == 0 ? xm : 0u;
+  // first cell / other three cells of the quad columns read: (i0, j), (i0, jp), (i0, jm)
+  const unsigned c0 = wx0 | wy, c1 = wy, p0 = wx0 | wyp, p1 = wyp, m0 = wx0 | wym, m1 = wym;
+  const unsigned wxp = (ixp == 0 ? xm : 0u) | wy, wxm = (ixm == 0 ? xm : 0u) | wy;
+  const float* __restrict__ vHx = v;
+  const float* __restrict__ vHy = v + nc;
+  const float* __restrict__ vHz = v + 2 * (int64_t)nc;
+  const float* __restrict__ vEx = v + 3 * (int64_t)nc;
+  const float* __restrict__ vEy = v + 4 * (int64_t)nc;
+  const float* __restrict__ vEz = v + 5 * (int64_t)nc;
+  const float* __restrict__ ie1 = ie + nc;
+  const float* __restrict__ ie2 = ie + 2 * (int64_t)nc;
+  const int km0 = k0 == 0 ? nz - 1 : k0 - 1;
+  unsigned zk = k0 == 0 ? zm : 0u;
+  int cell = col + k0 * nxy;
+  const int ckm0 = col + km0 * nxy;
+  const unsigned zkm0 = km0 == 0 ? zm : 0u;
+  float4 Hx_km = ldw4(vHx, ckm0, c0 | zkm0, c1 | zkm0, 0), Hy_km = ldw4(vHy, ckm0, c0 | zkm0, c1 | zkm0, 1);
+  float4 Ex = ldw4(vEx, cell, c0 | zk, c1 | zk, 3), Ey = ldw4(vEy, cell, c0 | zk, c1 | zk, 4);
+  for (int k = k0; k < k1; ++k, cell += nxy) {
+    const int kp = k + 1 == nz ? 0 : k + 1;
+    const unsigned zkp = kp == 0 ? zm : 0u;
+    const int ckp = col + kp * nxy;
+    const float4 Hx = ldw4(vHx, cell, c0 | zk, c1 | zk, 0), Hy = ldw4(vHy, cell, c0 | zk, c1 | zk, 1);
+    const float4 Hz = ldw4(vHz, cell, c0 | zk, c1 | zk, 2), Ez = ldw4(vEz, cell, c0 | zk, c1 | zk, 5);
+    const float4 Ex_kp = ldw4(vEx, ckp, c0 | zkp, c1 | zkp, 3), Ey_kp = ldw4(vEy, ckp, c0 | zkp, c1 | zkp, 4);
+    const float4 Ez_jp = ldw4(vEz, cell + djp, p0 | zk, p1 | zk, 5);
+    const float4 Ex_jp = ldw4(vEx, cell + djp, p0 | zk, p1 | zk, 3);
+    const float4 Hz_jm = ldw4(vHz, cell + djm, m0 | zk, m1 | zk, 2);
+    const float4 Hx_jm = ldw4(vHx, cell + djm, m0 | zk, m1 | zk, 0);
+    const float Ez_n = ldw(vEz, cell + dxp, wxp | zk, 5), Ey_n = ldw(vEy, cell + dxp, wxp | zk, 4);
+    const float Hz_p = ldw(vHz, cell + dxm, wxm | zk, 2), Hy_p = ldw(vHy, cell + dxm, wxm | zk, 1);
+    const float4 ie0q = ld4(ie + cell), ie1q = ld4(ie1 + cell), ie2q = ld4(ie2 + cell);
+    float4 out[6];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int li = g.la == 0 ? i0 + e : (g.la == 1 ? j : k);
+      float sg[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) sg[c] = sig2[2 * li + g.sighalf[c]];
+      const float ez = f4(Ez, e), ey = f4(Ey, e), ex = f4(Ex, e);
+      const float hx = f4(Hx, e), hy = f4(Hy, e), hz = f4(Hz, e);
+      const float ez_ip = e < 3 ? f4(Ez, e + 1) : Ez_n;
+      const float ey_ip = e < 3 ? f4(Ey, e + 1) : Ey_n;
+      const float hz_im = e > 0 ? f4(Hz, e - 1) : Hz_p;
+      const float hy_im = e > 0 ? f4(Hy, e - 1) : Hy_p;
+      const float cHx = (hz - f4(Hz_jm, e)) - (hy - f4(Hy_km, e));
+      const float cHy = (hx - f4(Hx_km, e)) - (hz - hz_im);
+      const float cHz = (hy - hy_im) - (hx - f4(Hx_jm, e));
+      float o[6];
+      o[0] = sg[0] * hx + ((f4(Ez_jp, e) - ez) - (f4(Ey_kp, e) - ey));
+      o[1] = sg[1] * hy + ((f4(Ex_kp, e) - ex) - (ez_ip - ez));
+      o[2] = sg[2] * hz + ((ey_ip - ey) - (f4(Ex_jp, e) - ex));
+      o[3] = f4(ie0q, e) * (sg[3] * ex - cHx);
+      o[4] = f4(ie1q, e) * (sg[4] * ey - cHy);
+      o[5] = f4(ie2q, e) * (sg[5] * ez - cHz);
+      const unsigned me = (e == 0 ? c0 : c1) | zk;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) set4(out[c], e, (me >> c) & 1u ? 0.f : o[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) *reinterpret_cast<float4*>(t + c * (int64_t)nc + cell) = out[c];
+    Hx_km = Hx;
+    Hy_km = Hy;
+    Ex = Ex_kp;
+    Ey = Ey_kp;
+    zk = zkp;
+  }
 }
 
 // L2 prefetch of the lines stencil_quad reads for a quad (its own six

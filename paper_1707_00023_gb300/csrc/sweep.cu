@@ -359,26 +359,36 @@ __device__ __forceinline__ void sw_apply4_body(const Geo& g, const Slot<float>& 
   if (j == 0) sw_apply_tail0<float>(s, w, ldh, btol, d0, d1, bid, nblk);
 }
 
-// Apply pass K_j for j >= 1, 3D FP32: SW_RED reducer blocks in front, then a
-// flat grid of one cell a thread (measured at 128^3, the stencil alone:
-// 30 us against 41 us for the persistent quad form at three blocks per SM).
-__global__ void __launch_bounds__(NTHREADS, 4) k_sw_apply1(Geo g, Slot<float> s, SwSlot w, int j, int64_t ld,
-                                                       const float* __restrict__ ie, const float* __restrict__ sig2,
-                                                       int ldh, int nbs, double btol) {
+// Apply pass K_j for j >= 1, 3D FP32: SW_RED reducer blocks in front, then
+// blocks of NTHREADS grid columns (quads of x-cells when QUAD, nx % 4 == 0),
+// block b covering planes kz (b / ncb) .. kz (b / ncb + 1) - 1 of its
+// columns, marching up in z (stencil_column_quad / stencil_column32: the
+// index work once per column, four of the eighteen neighbour values a cell
+// carried from the plane below).  Against one cell a thread with its
+// per-cell index and wall arithmetic (ALU pipe at 70 % of peak), 128^3
+// alone: 27-30 us (quads) and 32-35 us (cells) against 51-53 us.
+template <bool QUAD>
+__global__ void __launch_bounds__(NTHREADS, QUAD ? 2 : 3)
+    k_sw_apply_col(Geo g, Slot<float> s, SwSlot w, int j, int64_t ld, const float* __restrict__ ie,
+                   const float* __restrict__ sig2, int ldh, int nbs, double btol, int ncb, int kz) {
   pdl_wait();
   if (s.st->done || s.st->retired) return;
   if ((int)blockIdx.x < SW_RED) {
     sw_reduce_fin<float>(s, w, j, ldh, nbs, btol, blockIdx.x);
     return;
   }
-  const int cell = ((int)blockIdx.x - SW_RED) * NTHREADS + (int)threadIdx.x;
-  if (cell < (int)g.ncell) {
+  const int b = (int)blockIdx.x - SW_RED;
+  const int zc = b / ncb;
+  const int q = (b - zc * ncb) * NTHREADS + (int)threadIdx.x;
+  const int ncol = QUAD ? (g.nx >> 2) * g.ny : g.nx * g.ny;
+  const int k0 = zc * kz, k1 = min(g.nz, k0 + kz);
+  if (q < ncol && k0 < k1) {
     const float* __restrict__ v = s.V + (int64_t)j * ld;
     float* __restrict__ t = (float*)w.t;
-    float o[6];
-    stencil_cell32(g, v, ie, sig2, cell, o);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) t[c * g.ncell + cell] = o[c];
+    if constexpr (QUAD)
+      stencil_column_quad(g, v, ie, sig2, t, q, k0, k1);
+    else
+      stencil_column32(g, v, ie, sig2, t, q, k0, k1);
   }
   pdl_trigger();
 }
@@ -987,6 +997,36 @@ static void sw_grids(kx_ctx* c, const void* fa, const void* fs, size_t smem_s, i
   *nb_sweep = reserve_grid(c, (int)std::min<int64_t>(rounds, gs[kind].load()), gs[kind].load());
 }
 
+// Grid of k_sw_apply_col: SW_RED reducer blocks, then ncb column blocks on
+// each of ceil(nz / kz) plane ranges, kz chosen so that every block finds a
+// slot in the first wave beside the reducers (and beside the CTAs that
+// concurrently running kernels keep resident).
+struct ColGrid {
+  int blocks, ncb, kz;
+};
+
+static ColGrid col_grid(kx_ctx* c, const void* kernel, bool quad) {
+  static std::atomic<int> occ_cache[2];
+  int occ = occ_cache[quad].load();
+  if (!occ) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, NTHREADS, 0) != cudaSuccess || occ < 1) {
+      cudaGetLastError();
+      occ = 1;
+    }
+    occ_cache[quad] = occ;
+  }
+  const Geo& g = c->geo;
+  const int full = c->nsm * occ;
+  const int avail = std::max(1, reserve_grid(c, full, full) - SW_RED);
+  const int64_t ncol = quad ? (int64_t)(g.nx / 4) * g.ny : (int64_t)g.nx * g.ny;
+  ColGrid r;
+  r.ncb = (int)((ncol + NTHREADS - 1) / NTHREADS);
+  const int64_t kz = ((int64_t)g.nz * r.ncb + avail - 1) / avail;
+  r.kz = (int)std::min<int64_t>(std::max<int64_t>(kz, 1), g.nz);
+  r.blocks = SW_RED + r.ncb * ((g.nz + r.kz - 1) / r.kz);
+  return r;
+}
+
 template <typename T, int DIM>
 static kx_status sweep_t(kx_ctx* c, int slot, int m) {
   const Geo& g = c->geo;
@@ -1000,8 +1040,8 @@ static kx_status sweep_t(kx_ctx* c, int slot, int m) {
   // the quad kernels need 16-byte aligned rows of every array they read
   constexpr bool f3 = sizeof(T) == 4 && DIM == 3;
   const bool quad = f3 && (g.nx % 4) == 0;
-  // steps j >= 1 apply A by the flat one-cell kernel (32-bit cell indices)
-  const bool flat = f3 && g.ncell + SW_RED * NTHREADS < ((int64_t)1 << 31);
+  // steps j >= 1 apply A by the column march (32-bit cell offsets)
+  const bool colm = f3 && g.ncell < ((int64_t)1 << 31);
   int nba = 0, nbs = 0;
   if (quad) {
     // per device, and before any launch (contexts of the multi-problem
@@ -1039,10 +1079,16 @@ static kx_status sweep_t(kx_ctx* c, int slot, int m) {
     if (j == m) {
       launch_k(c, k_sw_last<T>, dim3(1), dim3(NTHREADS), 0, c->stream, s, w, m, ldh, nbs, bt);
     } else if constexpr (f3) {
-      if (j >= 1 && flat)
-        launch_k(c, k_sw_apply1, dim3(SW_RED + (int)((g.ncell + NTHREADS - 1) / NTHREADS)), dim3(NTHREADS), 0,
-                 c->stream, g, (Slot<float>)s, w, j, c->ld, (const float*)ie, (const float*)sg, ldh, nbs, bt);
-      else if (quad)
+      if (j >= 1 && colm) {
+        const void* kc = quad ? (const void*)k_sw_apply_col<true> : (const void*)k_sw_apply_col<false>;
+        const ColGrid cg = col_grid(c, kc, quad);
+        if (quad)
+          launch_k(c, k_sw_apply_col<true>, dim3(cg.blocks), dim3(NTHREADS), 0, c->stream, g, (Slot<float>)s, w, j,
+                   c->ld, (const float*)ie, (const float*)sg, ldh, nbs, bt, cg.ncb, cg.kz);
+        else
+          launch_k(c, k_sw_apply_col<false>, dim3(cg.blocks), dim3(NTHREADS), 0, c->stream, g, (Slot<float>)s, w,
+                   j, c->ld, (const float*)ie, (const float*)sg, ldh, nbs, bt, cg.ncb, cg.kz);
+      } else if (quad)
         launch_k(c, k_sw_apply4, dim3(ga), dim3(NTHREADS), 0, c->stream, g, (Slot<float>)s, w, j, c->ld,
                  (const float*)ie, (const float*)sg, ldh, nbs, bt);
       else
