@@ -500,33 +500,106 @@ __device__ __forceinline__ void stencil_column_quad(const Geo& g, const float* _
   }
 }
 
-// L2 prefetch of the lines stencil_quad reads for a quad (its own six
-// components, the y and z neighbours it uses, the three 1/eps rows): issued
-// one quad (or tile) ahead, it lets a latency-bound loop keep the next
-// round's DRAM traffic in flight.  q must be a quad of the grid.
+// stencil_quad on the quad whose first cell is c0 (a multiple of 4, nx % 4
+// == 0, ncell < 2^31), with 32-bit index arithmetic and the wall tests as
+// per-component bit masks (the same operations on the field values, so the
+// same bits); the sigma values are read once per quad unless the layer axis
+// is x.  At the start of each tile of the single sweep this is the part that
+// keeps the block from streaming; the 64-bit divisions and per-value wall
+// tests of stencil_quad made it about twice as long.
+__device__ __forceinline__ void stencil_quad32(const Geo& g, const float* __restrict__ v, const float* __restrict__ ie,
+                                               const float* __restrict__ sig2, int c0, float4 out[6]) {
+  const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny, nc = (int)g.ncell;
+  const unsigned r = (unsigned)c0 / (unsigned)nx;
+  const int i0 = c0 - (int)r * nx;
+  const unsigned kq = r / (unsigned)ny;
+  const int jj = (int)r - (int)kq * ny, kk = (int)kq;
+  const int jp = (jj + 1 == ny) ? 0 : jj + 1, jm = (jj == 0) ? ny - 1 : jj - 1;
+  const int kp = (kk + 1 == nz) ? 0 : kk + 1, km = (kk == 0) ? nz - 1 : kk - 1;
+  const int cjp = c0 + (jp - jj) * nx, cjm = c0 + (jm - jj) * nx;
+  const int ckp = c0 + (kp - kk) * nxy, ckm = c0 + (km - kk) * nxy;
+  const int ixp = (i0 + 4 == nx) ? 0 : i0 + 4, ixm = (i0 == 0) ? nx - 1 : i0 - 1;
+  const int cxp = c0 - i0 + ixp, cxm = c0 - i0 + ixm;
+  const unsigned xm = wall_bits(g, 0), ym = wall_bits(g, 1), zm = wall_bits(g, 2);
+  const unsigned wx0 = i0 == 0 ? xm : 0u, wy = jj == 0 ? ym : 0u, wz = kk == 0 ? zm : 0u;
+  const unsigned wyp = jp == 0 ? ym : 0u, wym = jm == 0 ? ym : 0u, wzp = kp == 0 ? zm : 0u, wzm = km == 0 ? zm : 0u;
+  const unsigned o0 = wx0 | wy | wz, o1 = wy | wz;   // the quad's first cell / the other three
+  const float* __restrict__ vHx = v;
+  const float* __restrict__ vHy = v + nc;
+  const float* __restrict__ vHz = v + 2 * (int64_t)nc;
+  const float* __restrict__ vEx = v + 3 * (int64_t)nc;
+  const float* __restrict__ vEy = v + 4 * (int64_t)nc;
+  const float* __restrict__ vEz = v + 5 * (int64_t)nc;
+  const float4 Hx = ldw4(vHx, c0, o0, o1, 0), Hy = ldw4(vHy, c0, o0, o1, 1), Hz = ldw4(vHz, c0, o0, o1, 2);
+  const float4 Ex = ldw4(vEx, c0, o0, o1, 3), Ey = ldw4(vEy, c0, o0, o1, 4), Ez = ldw4(vEz, c0, o0, o1, 5);
+  const float4 Ez_jp = ldw4(vEz, cjp, wx0 | wyp | wz, wyp | wz, 5), Ex_jp = ldw4(vEx, cjp, wx0 | wyp | wz, wyp | wz, 3);
+  const float4 Ey_kp = ldw4(vEy, ckp, wx0 | wy | wzp, wy | wzp, 4), Ex_kp = ldw4(vEx, ckp, wx0 | wy | wzp, wy | wzp, 3);
+  const float4 Hz_jm = ldw4(vHz, cjm, wx0 | wym | wz, wym | wz, 2), Hx_jm = ldw4(vHx, cjm, wx0 | wym | wz, wym | wz, 0);
+  const float4 Hy_km = ldw4(vHy, ckm, wx0 | wy | wzm, wy | wzm, 1), Hx_km = ldw4(vHx, ckm, wx0 | wy | wzm, wy | wzm, 0);
+  const unsigned wxp = (ixp == 0 ? xm : 0u) | wy | wz, wxm = (ixm == 0 ? xm : 0u) | wy | wz;
+  const float Ez_n = ldw(vEz, cxp, wxp, 5), Ey_n = ldw(vEy, cxp, wxp, 4);
+  const float Hz_p = ldw(vHz, cxm, wxm, 2), Hy_p = ldw(vHy, cxm, wxm, 1);
+  const float4 ie0 = ld4(ie + c0), ie1 = ld4(ie + nc + c0), ie2 = ld4(ie + 2 * (int64_t)nc + c0);
+  float sgq[6];
+  if (g.la != 0) {
+    const int li = g.la == 1 ? jj : kk;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sgq[c] = sig2[2 * li + g.sighalf[c]];
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    float sg[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sg[c] = g.la == 0 ? sig2[2 * (i0 + e) + g.sighalf[c]] : sgq[c];
+    const float ez = f4(Ez, e), ey = f4(Ey, e), ex = f4(Ex, e);
+    const float hx = f4(Hx, e), hy = f4(Hy, e), hz = f4(Hz, e);
+    const float ez_ip = e < 3 ? f4(Ez, e + 1) : Ez_n;
+    const float ey_ip = e < 3 ? f4(Ey, e + 1) : Ey_n;
+    const float hz_im = e > 0 ? f4(Hz, e - 1) : Hz_p;
+    const float hy_im = e > 0 ? f4(Hy, e - 1) : Hy_p;
+    const float cHx = (hz - f4(Hz_jm, e)) - (hy - f4(Hy_km, e));
+    const float cHy = (hx - f4(Hx_km, e)) - (hz - hz_im);
+    const float cHz = (hy - hy_im) - (hx - f4(Hx_jm, e));
+    float o[6];
+    o[0] = sg[0] * hx + ((f4(Ez_jp, e) - ez) - (f4(Ey_kp, e) - ey));
+    o[1] = sg[1] * hy + ((f4(Ex_kp, e) - ex) - (ez_ip - ez));
+    o[2] = sg[2] * hz + ((ey_ip - ey) - (f4(Ex_jp, e) - ex));
+    o[3] = f4(ie0, e) * (sg[3] * ex - cHx);
+    o[4] = f4(ie1, e) * (sg[4] * ey - cHy);
+    o[5] = f4(ie2, e) * (sg[5] * ez - cHz);
+    const unsigned me = e == 0 ? o0 : o1;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) set4(out[c], e, (me >> c) & 1u ? 0.f : o[c]);
+  }
+}
+
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
-__device__ __forceinline__ void prefetch_quad(const Geo& g, const float* v, const float* ie, const Quad& q) {
-  const int64_t nc = g.ncell;
-  const int64_t nxy = (int64_t)g.nx * g.ny;
-  const int64_t c0 = q.c0;
-  const int jj = q.jj, kk = q.kk;
-  const int jp = (jj + 1 == g.ny) ? 0 : jj + 1, jm = (jj == 0) ? g.ny - 1 : jj - 1;
-  const int kp = (kk + 1 == g.nz) ? 0 : kk + 1, km = (kk == 0) ? g.nz - 1 : kk - 1;
-  const int64_t cjp = c0 + (int64_t)(jp - jj) * g.nx, cjm = c0 + (int64_t)(jm - jj) * g.nx;
-  const int64_t ckp = c0 + (int64_t)(kp - kk) * nxy, ckm = c0 + (int64_t)(km - kk) * nxy;
+// L2 prefetch of the lines stencil_quad32 reads for the quad whose first
+// cell is c0 (its own six components, the y and z neighbours it uses, the
+// three 1/eps rows): issued a tile ahead, it lets the single sweep keep the
+// next tile's stencil loads off DRAM.  32-bit index arithmetic (ncell < 2^31).
+__device__ __forceinline__ void prefetch_quad32(const Geo& g, const float* v, const float* ie, int c0) {
+  const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny, nc = (int)g.ncell;
+  const unsigned r = (unsigned)c0 / (unsigned)nx;
+  const unsigned kq = r / (unsigned)ny;
+  const int jj = (int)r - (int)kq * ny, kk = (int)kq;
+  const int jp = (jj + 1 == ny) ? 0 : jj + 1, jm = (jj == 0) ? ny - 1 : jj - 1;
+  const int kp = (kk + 1 == nz) ? 0 : kk + 1, km = (kk == 0) ? nz - 1 : kk - 1;
+  const int cjp = c0 + (jp - jj) * nx, cjm = c0 + (jm - jj) * nx;
+  const int ckp = c0 + (kp - kk) * nxy, ckm = c0 + (km - kk) * nxy;
 #pragma unroll
-  for (int c = 0; c < 6; ++c) prefetch_l2(v + c * nc + c0);
-  prefetch_l2(v + 5 * nc + cjp);
-  prefetch_l2(v + 3 * nc + cjp);
-  prefetch_l2(v + 4 * nc + ckp);
-  prefetch_l2(v + 3 * nc + ckp);
-  prefetch_l2(v + 2 * nc + cjm);
+  for (int c = 0; c < 6; ++c) prefetch_l2(v + c * (int64_t)nc + c0);
+  prefetch_l2(v + 5 * (int64_t)nc + cjp);
+  prefetch_l2(v + 3 * (int64_t)nc + cjp);
+  prefetch_l2(v + 4 * (int64_t)nc + ckp);
+  prefetch_l2(v + 3 * (int64_t)nc + ckp);
+  prefetch_l2(v + 2 * (int64_t)nc + cjm);
   prefetch_l2(v + cjm);
   prefetch_l2(v + nc + ckm);
   prefetch_l2(v + ckm);
 #pragma unroll
-  for (int e = 0; e < 3; ++e) prefetch_l2(ie + e * nc + c0);
+  for (int e = 0; e < 3; ++e) prefetch_l2(ie + e * (int64_t)nc + c0);
 }
 
 }  // namespace kx

@@ -708,10 +708,9 @@ __device__ __forceinline__ void sw_pass4s_body(const Geo& g, const Slot<float>& 
       act = q4 < nq;
       c0 = 0;
       if (act) {
-        const Quad qd = make_quad(g, q4);
-        c0 = qd.c0;
+        c0 = q4 << 2;
         float4 at[6];
-        stencil_quad(g, t, ie, sig2, qd, at);
+        stencil_quad32(g, t, ie, sig2, (int)c0, at);
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
           const float4 tv = ld4(t + c * nc + c0);
@@ -732,7 +731,7 @@ __device__ __forceinline__ void sw_pass4s_body(const Geo& g, const Slot<float>& 
     if (ends) {
       // prefetch the next tile's stencil inputs
       const int64_t qn = (tile + nblk) * NTHREADS + threadIdx.x;
-      if (qn < nq) prefetch_quad(g, t, ie, make_quad(g, qn));
+      if (qn < nq) prefetch_quad32(g, t, ie, (int)(qn << 2));
     }
 #pragma unroll 1
     for (int q = 0; q < cnt; ++q) {
@@ -1039,7 +1038,7 @@ static kx_status sweep_t(kx_ctx* c, int slot, int m) {
   const double bt = sw_btol<T>();
   // the quad kernels need 16-byte aligned rows of every array they read
   constexpr bool f3 = sizeof(T) == 4 && DIM == 3;
-  const bool quad = f3 && (g.nx % 4) == 0;
+  const bool quad = f3 && (g.nx % 4) == 0 && g.ncell < ((int64_t)1 << 31);
   // steps j >= 1 apply A by the column march (32-bit cell offsets)
   const bool colm = f3 && g.ncell < ((int64_t)1 << 31);
   int nba = 0, nbs = 0;
