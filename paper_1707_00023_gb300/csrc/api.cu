@@ -1122,7 +1122,20 @@ kx_status response_restart_dim(kx_ctx* c, const void* d_g, const double* omegas,
       if (h_states[f] == 0 || h_states[f] == 1) rcount[f] = k;
       all_stopped = all_stopped && h_states[f] != 0;
     }
-    if (all_stopped || k >= kmax) break;
+    if (all_stopped || k >= kmax) {
+      if (ovl && k < kmax) {
+        // restart k + 1's process runs speculatively in the other slot and is
+        // not needed: its next step's finalisation stops it, and the launches
+        // still queued return at entry; the request lands before the context
+        // stream continues (it waits for the auxiliary stream below)
+        int* one = reinterpret_cast<int*>(c->h_small + 255);
+        *one = 1;
+        SlotState* st_nx = c->d_state + (sl ^ 1);
+        KX_CUDA(c, cudaMemcpyAsync(&st_nx->abort, one, sizeof(int), cudaMemcpyHostToDevice, Bs), "stop request");
+        KX_CUDA(c, cudaEventRecord(c->ev_proj[sl], Bs), "event record");
+      }
+      break;
+    }
     if (!ovl) {
       // the next basis starts from v_{m+1} (same slot, column m_done -> 0)
       KX_TRY(launch_rst_nextvec(c, A, 0, 0));

@@ -53,7 +53,16 @@ struct SlotState {
   int substeps;
   int expm_evals;
   int retired;       // final combination done: every later kernel skips this slot
+  int abort;         // set by the host while a process runs: the next step's
+                     // finalisation stops it (done = 1), so the launches after
+                     // it skip the slot (a speculative process found unneeded)
 };
+
+// The host's stop request of a running Arnoldi process, read by the block
+// that finalises a step (it may land at any time: read past the caches).
+__device__ __forceinline__ bool abort_requested(const SlotState* st) {
+  return *reinterpret_cast<const volatile int*>(&st->abort) != 0;
+}
 
 // Pointers of one slot's workspace.
 template <typename T>

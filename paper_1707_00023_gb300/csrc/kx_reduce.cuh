@@ -93,7 +93,7 @@ __device__ __forceinline__ bool fin_prev_b(const Slot<T>& s, int j, int ldh, int
       s.st->m_done = j;
       s.scale[j] = scl;
       if (stp == 2) s.st->status = KX_ENONFINITE;
-      if (stp) s.st->done = 1;
+      if (stp || abort_requested(s.st)) s.st->done = 1;
     }
     res = scl;
     stop = stp;

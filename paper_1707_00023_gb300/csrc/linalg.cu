@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(NTHREADS) k_fin_b(SlotSet<T> ss, int j, int ld
     const double h = sqrt(tot);
     s.H[(j + 1) + (int64_t)j * ldh] = h;
     s.st->m_done = j + 1;
+    if (abort_requested(s.st)) s.st->done = 1;
     if (!isfinite(h)) {
       s.st->status = KX_ENONFINITE;
       s.st->done = 1;

@@ -137,7 +137,7 @@ __device__ void sw_fin(const Slot<T>& s, SwCoef* co, double* G, int j, int ldh, 
     s.scale[j] = sig;
     st->m_done = j;
     if (stop == 2) st->status = KX_ENONFINITE;
-    if (stop) st->done = 1;
+    if (stop || abort_requested(st)) st->done = 1;
     sh_H[j + (j - 1) * LG] = b;
     sh_beta = b;
     sh_sig = sig;
