@@ -239,6 +239,7 @@ struct kx_ctx {
   int64_t rst_plane_max = 0;     // plane nodes the accumulators hold per frequency
   cudaStream_t aux_stream = nullptr;   // projected work overlapping the next Arnoldi process
   int side_ctas = 0;        // long-lived CTAs of other kernels sharing the SMs meanwhile
+  int side_steps = 1 << 30; // leading steps of each Arnoldi process that the side CTAs may overlap
   int pdl = 0;              // launch the Arnoldi chain with programmatic dependent launch
   // single-sweep Arnoldi workspace (per slot, and one shared vector)
   void* d_swT = nullptr;
@@ -391,6 +392,12 @@ inline void launch_k(const kx_ctx* c, void (*kern)(KArgs...), dim3 grid, dim3 bl
 inline int reserve_grid(const kx_ctx* c, int nb, int gr) {
   if (c->side_ctas <= 0) return nb;
   return std::min(nb, std::max(c->nsm, gr - c->side_ctas));
+}
+
+// The same for the launches of Arnoldi step j: the side CTAs are only
+// expected beside the first side_steps steps of a process.
+inline int reserve_grid_at(const kx_ctx* c, int nb, int gr, int j) {
+  return j < c->side_steps ? reserve_grid(c, nb, gr) : nb;
 }
 
 // Timing brackets around one launch (no-ops unless timing is on).

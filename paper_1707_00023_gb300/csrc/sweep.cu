@@ -986,25 +986,28 @@ static SwSlot sw_slot(kx_ctx* c, int slot) {
 
 // Persistent grids (occupancy x SMs, capped by the work and the partial
 // stride), shrunk for resident CTAs of kernels running beside the process.
+// nb_sweep_late: the sweep grid of the steps past the side CTAs' window.
 static void sw_grids(kx_ctx* c, const void* fa, const void* fs, size_t smem_s, int kind, int64_t items,
-                     int* nb_apply, int* nb_sweep) {
+                     int* nb_apply, int* nb_sweep, int* nb_sweep_late) {
   static std::atomic<int> ga[8], gs[8];
   if (!ga[kind]) ga[kind] = persistent_grid(c, fa, 1 << 30, 0);
   if (!gs[kind]) gs[kind] = persistent_grid(c, fs, 1 << 30, smem_s);
   const int64_t rounds = (items + NTHREADS - 1) / NTHREADS;
   *nb_apply = reserve_grid(c, (int)std::min<int64_t>(rounds, ga[kind].load()), ga[kind].load());
-  *nb_sweep = reserve_grid(c, (int)std::min<int64_t>(rounds, gs[kind].load()), gs[kind].load());
+  const int ns = (int)std::min<int64_t>(rounds, gs[kind].load());
+  *nb_sweep = reserve_grid(c, ns, gs[kind].load());
+  *nb_sweep_late = reserve_grid_at(c, ns, gs[kind].load(), c->side_steps);
 }
 
-// Grid of k_sw_apply_col: SW_RED reducer blocks, then ncb column blocks on
-// each of ceil(nz / kz) plane ranges, kz chosen so that every block finds a
-// slot in the first wave beside the reducers (and beside the CTAs that
-// concurrently running kernels keep resident).
+// Grid of k_sw_apply_col for step j: SW_RED reducer blocks, then ncb column
+// blocks on each of ceil(nz / kz) plane ranges, kz chosen so that every
+// block finds a slot in the first wave beside the reducers (and, in the
+// steps the side CTAs may overlap, beside them).
 struct ColGrid {
   int blocks, ncb, kz;
 };
 
-static ColGrid col_grid(kx_ctx* c, const void* kernel, bool quad) {
+static ColGrid col_grid(kx_ctx* c, const void* kernel, bool quad, int j) {
   static std::atomic<int> occ_cache[2];
   int occ = occ_cache[quad].load();
   if (!occ) {
@@ -1016,7 +1019,7 @@ static ColGrid col_grid(kx_ctx* c, const void* kernel, bool quad) {
   }
   const Geo& g = c->geo;
   const int full = c->nsm * occ;
-  const int avail = std::max(1, reserve_grid(c, full, full) - SW_RED);
+  const int avail = std::max(1, reserve_grid_at(c, full, full, j) - SW_RED);
   const int64_t ncol = quad ? (int64_t)(g.nx / 4) * g.ny : (int64_t)g.nx * g.ny;
   ColGrid r;
   r.ncb = (int)((ncol + NTHREADS - 1) / NTHREADS);
@@ -1041,32 +1044,34 @@ static kx_status sweep_t(kx_ctx* c, int slot, int m) {
   const bool quad = f3 && (g.nx % 4) == 0 && g.ncell < ((int64_t)1 << 31);
   // steps j >= 1 apply A by the column march (32-bit cell offsets)
   const bool colm = f3 && g.ncell < ((int64_t)1 << 31);
-  int nba = 0, nbs = 0;
+  int nba = 0, nbs = 0, nbs_late = 0;
   if (quad) {
     // per device, and before any launch (contexts of the multi-problem
     // driver run on several host threads)
     static SmemOptIn smem{};
     const kx_status so = smem_opt_in(c, smem, (const void*)k_sw_pass4s, SW_SMEM);
     if (so != KX_OK) return so;
-    sw_grids(c, (const void*)k_sw_apply4, (const void*)k_sw_pass4s, SW_SMEM, 7, g.ncell / 4, &nba, &nbs);
+    sw_grids(c, (const void*)k_sw_apply4, (const void*)k_sw_pass4s, SW_SMEM, 7, g.ncell / 4, &nba, &nbs, &nbs_late);
   } else {
     sw_grids(c, (const void*)k_sw_apply<T, DIM, TableMat<T>>, (const void*)k_sw_pass<T, DIM, TableMat<T>>, 0,
-             (sizeof(T) == 8 ? 3 : 0) + (DIM - 2), g.ncell, &nba, &nbs);
+             (sizeof(T) == 8 ? 3 : 0) + (DIM - 2), g.ncell, &nba, &nbs, &nbs_late);
   }
   const double vb = (double)c->n * c->esize;
   const double mb = (double)g.ne * g.ncell * c->esize;
   for (int j = 0; j <= m; ++j) {
+    // sweep S_j's grid; apply pass K_j's reducers and k_sw_last take its partials
+    const int nbs_j = j < c->side_steps ? nbs : nbs_late;
     if (j >= 1) {
       time_begin(c);
       if constexpr (f3) {
         if (quad)
-          launch_k(c, k_sw_pass4s, dim3(nbs), dim3(NTHREADS), SW_SMEM, c->stream, g, (Slot<float>)s, w, j, c->ld,
+          launch_k(c, k_sw_pass4s, dim3(nbs_j), dim3(NTHREADS), SW_SMEM, c->stream, g, (Slot<float>)s, w, j, c->ld,
                    (const float*)ie, (const float*)sg);
         else
-          launch_k(c, k_sw_pass<T, DIM, TableMat<T>>, dim3(nbs), dim3(NTHREADS), 0, c->stream, g, s, w, j, c->ld,
+          launch_k(c, k_sw_pass<T, DIM, TableMat<T>>, dim3(nbs_j), dim3(NTHREADS), 0, c->stream, g, s, w, j, c->ld,
                    mat);
       } else {
-        launch_k(c, k_sw_pass<T, DIM, TableMat<T>>, dim3(nbs), dim3(NTHREADS), 0, c->stream, g, s, w, j, c->ld, mat);
+        launch_k(c, k_sw_pass<T, DIM, TableMat<T>>, dim3(nbs_j), dim3(NTHREADS), 0, c->stream, g, s, w, j, c->ld, mat);
       }
       time_end(c, KX_K_SWEEP, (j + 2.0) * vb + mb);
       KX_CHECK_LAUNCH(c);
@@ -1076,26 +1081,26 @@ static kx_status sweep_t(kx_ctx* c, int slot, int m) {
     const int ga = j == 0 ? nba : (nba > 2 * SW_RED ? nba - SW_RED : nba) + SW_RED;
     time_begin(c);
     if (j == m) {
-      launch_k(c, k_sw_last<T>, dim3(1), dim3(NTHREADS), 0, c->stream, s, w, m, ldh, nbs, bt);
+      launch_k(c, k_sw_last<T>, dim3(1), dim3(NTHREADS), 0, c->stream, s, w, m, ldh, nbs_j, bt);
     } else if constexpr (f3) {
       if (j >= 1 && colm) {
         const void* kc = quad ? (const void*)k_sw_apply_col<true> : (const void*)k_sw_apply_col<false>;
-        const ColGrid cg = col_grid(c, kc, quad);
+        const ColGrid cg = col_grid(c, kc, quad, j);
         if (quad)
           launch_k(c, k_sw_apply_col<true>, dim3(cg.blocks), dim3(NTHREADS), 0, c->stream, g, (Slot<float>)s, w, j,
-                   c->ld, (const float*)ie, (const float*)sg, ldh, nbs, bt, cg.ncb, cg.kz);
+                   c->ld, (const float*)ie, (const float*)sg, ldh, nbs_j, bt, cg.ncb, cg.kz);
         else
           launch_k(c, k_sw_apply_col<false>, dim3(cg.blocks), dim3(NTHREADS), 0, c->stream, g, (Slot<float>)s, w,
-                   j, c->ld, (const float*)ie, (const float*)sg, ldh, nbs, bt, cg.ncb, cg.kz);
+                   j, c->ld, (const float*)ie, (const float*)sg, ldh, nbs_j, bt, cg.ncb, cg.kz);
       } else if (quad)
         launch_k(c, k_sw_apply4, dim3(ga), dim3(NTHREADS), 0, c->stream, g, (Slot<float>)s, w, j, c->ld,
-                 (const float*)ie, (const float*)sg, ldh, nbs, bt);
+                 (const float*)ie, (const float*)sg, ldh, nbs_j, bt);
       else
         launch_k(c, k_sw_apply<T, DIM, TableMat<T>>, dim3(ga), dim3(NTHREADS), 0, c->stream, g, s, w, j, c->ld, mat,
-                 ldh, nbs, bt);
+                 ldh, nbs_j, bt);
     } else {
       launch_k(c, k_sw_apply<T, DIM, TableMat<T>>, dim3(ga), dim3(NTHREADS), 0, c->stream, g, s, w, j, c->ld, mat,
-               ldh, nbs, bt);
+               ldh, nbs_j, bt);
     }
     time_end(c, KX_K_SWAPPLY, j < m ? 2.0 * vb + mb : 0.0);
     KX_CHECK_LAUNCH(c);
