@@ -1010,10 +1010,12 @@ kx_status response_restart_dim(kx_ctx* c, const void* d_g, const double* omegas,
   } side{c};
   c->side_ctas = nfreq + 1;
   // the projected work of a restart (set-up, cascade, ...) runs beside the
-  // first steps of the next process; in the later steps the Arnoldi launches
-  // take every SM slot (measured on the single sweep: half the steps covers
-  // it at 96^3 and 128^3, and 128^3 runs 4.5 % faster than with the
-  // reservation throughout; a fixed rule, so every mode has the same grids)
+  // first steps of the next process; in the later steps the single-sweep
+  // launches take every SM slot (half the steps covers it at 96^3 and
+  // 128^3, where this runs 3-6 % faster than keeping the reservation
+  // throughout).  The two-pass form, used on smaller grids whose processes
+  // are shorter than the projected work, keeps it for every step.  A fixed
+  // rule, so every mode has the same grids and bits.
   c->side_steps = (c->m + 1) / 2;
   // the Arnoldi chain of this method runs with programmatic dependent launch
   c->pdl = 1;
