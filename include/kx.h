@@ -345,8 +345,9 @@ kx_status response_at_freqs_multi(kx_ctx* const* ctxs, int nctx, const void* con
  * cuda_stream: the stream of the batched launches (or KX_OWN_STREAM).
  * Creation allocates a small table and chooses how each launch is split
  * (an autotuner times an Arnoldi process of min(12, krylov_dim) steps of the whole batch for each
- * candidate granularity -- sweep tiles per block 1..16, stencil rounds per
- * apply thread 1..4 -- and keeps the fastest; the choice is cached per size
+ * candidate granularity -- sweep tiles per block 1..16, apply work per thread
+ * r = 1, 2, 4 (step 0: r quad rounds; later steps: 2 r planes a thread in the
+ * column march) -- and keeps the fastest; the choice is cached per size
  * class, the multiset of the problems' grids, for the rest of the process).
  * The timing runs overwrite basis slot 0 of every context.
  * Errors: KX_EINVAL (arguments, a context that does not qualify), KX_ENOMEM,
@@ -357,7 +358,8 @@ typedef struct {
   int sweep_tiles_per_block;    /* the autotuner's choice                      */
   int apply_rounds_per_thread;  /* the autotuner's choice                      */
   int sweep_blocks;             /* blocks of one batched sweep launch          */
-  int apply_blocks;             /* blocks of one batched apply launch          */
+  int apply_blocks;             /* blocks of one batched apply launch, steps
+                                   j >= 1 (the column march)                   */
   int from_cache;               /* 1: the choice came from an earlier batch    */
   double tune_ms;               /* time the timing runs took (0 if cached)     */
   int64_t batched_launches;     /* batched Arnoldi launches so far             */

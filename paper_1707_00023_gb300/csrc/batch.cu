@@ -37,10 +37,10 @@ struct kx_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<SwInst> tab;
-  std::vector<int> aoff, soff;   // block offsets of the apply and sweep launches (n + 1 each)
+  std::vector<int> aoff, soff, coff;   // block offsets of the step-0 apply, sweep and column apply launches
   SwInst* d_tab = nullptr;
-  int* d_off = nullptr;          // aoff then soff
-  int na = 0, ns = 0;            // launch totals
+  int* d_off = nullptr;          // aoff, soff, coff (n + 1 each)
+  int na = 0, ns = 0, nc = 0;    // launch totals
   int tpb = 0, rpt = 0;          // chosen granularity: sweep tiles per block, apply rounds per thread
   int from_cache = 0;
   double tune_ms = 0.0;
@@ -125,12 +125,14 @@ struct StreamSwap {
 };
 
 // Launch split for a granularity: problem i gets ns_i = ceil(tiles_i / tpb)
-// sweep blocks and SW_RED + ceil(quads_i / (NTHREADS rpt)) apply blocks,
-// each capped by its partial-sum stride.
+// sweep blocks, SW_RED + ceil(quads_i / (NTHREADS rpt)) step-0 apply blocks,
+// each capped by its partial-sum stride, and SW_RED + ncb_i ceil(nz_i / kz)
+// column-march apply blocks with kz = 2 rpt planes a block.
 kx_status set_grids(kx_batch* b, int tpb, int rpt) {
   const int n = (int)b->ctx.size();
   b->aoff.assign(n + 1, 0);
   b->soff.assign(n + 1, 0);
+  b->coff.assign(n + 1, 0);
   for (int i = 0; i < n; ++i) {
     kx_ctx* c = b->ctx[i];
     const int64_t ntiles = (c->geo.ncell + SW_TILE - 1) / SW_TILE;
@@ -145,9 +147,16 @@ kx_status set_grids(kx_batch* b, int tpb, int rpt) {
     I.na = SW_RED + nst;
     b->soff[i + 1] = b->soff[i] + ns;
     b->aoff[i + 1] = b->aoff[i] + I.na;
+    const int64_t ncol = (int64_t)(c->geo.nx / 4) * c->geo.ny;
+    I.ncb = (int)((ncol + NTHREADS - 1) / NTHREADS);
+    I.kz = std::min(c->geo.nz, 2 * rpt);
+    I.c0 = b->coff[i];
+    I.nc = SW_RED + I.ncb * ((c->geo.nz + I.kz - 1) / I.kz);
+    b->coff[i + 1] = b->coff[i] + I.nc;
   }
   b->na = b->aoff[n];
   b->ns = b->soff[n];
+  b->nc = b->coff[n];
   b->tpb = tpb;
   b->rpt = rpt;
   KB_CUDA(b, cudaMemcpyAsync(b->d_tab, b->tab.data(), sizeof(SwInst) * n, cudaMemcpyHostToDevice, b->stream),
@@ -155,6 +164,9 @@ kx_status set_grids(kx_batch* b, int tpb, int rpt) {
   KB_CUDA(b, cudaMemcpyAsync(b->d_off, b->aoff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->stream),
           "offset upload");
   KB_CUDA(b, cudaMemcpyAsync(b->d_off + n + 1, b->soff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice,
+                             b->stream),
+          "offset upload");
+  KB_CUDA(b, cudaMemcpyAsync(b->d_off + 2 * (n + 1), b->coff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice,
                              b->stream),
           "offset upload");
   KB_CUDA(b, cudaStreamSynchronize(b->stream), "offset upload");
@@ -177,8 +189,9 @@ double sweep_bytes_of(const kx_batch* b, int j, const std::vector<char>* active)
 kx_status arnoldi_all(kx_batch* b, int slot, const std::vector<char>* active = nullptr) {
   const int n = (int)b->ctx.size();
   const size_t before = b->sweep_events.size();
-  const kx_status st = sweep_arnoldi_batch(b->ctx[0], b->stream, b->d_tab, b->d_off, b->d_off + n + 1, n, b->na,
-                                           b->ns, slot, b->ctx[0]->m, &b->launches,
+  const kx_status st = sweep_arnoldi_batch(b->ctx[0], b->stream, b->d_tab, b->d_off, b->d_off + n + 1,
+                                           b->d_off + 2 * (n + 1), n, b->na, b->ns, b->nc, slot, b->ctx[0]->m,
+                                           &b->launches,
                                            b->timing ? &b->sweep_events : nullptr);
   if (b->timing)
     for (size_t k = before; k < b->sweep_events.size(); ++k)
@@ -344,7 +357,7 @@ kx_status kx_batch_create(kx_ctx* const* ctxs, int nctx, void* cuda_stream, kx_b
     b->stream = (cudaStream_t)cuda_stream;
   }
   if (cudaMalloc(&b->d_tab, sizeof(SwInst) * nctx) != cudaSuccess ||
-      cudaMalloc(&b->d_off, sizeof(int) * 2 * (nctx + 1)) != cudaSuccess ||
+      cudaMalloc(&b->d_off, sizeof(int) * 3 * (nctx + 1)) != cudaSuccess ||
       cudaMallocHost(&b->h_pin, sizeof(int) * (nctx * (MAXF + 1) + 1)) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_arn, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
@@ -405,7 +418,7 @@ kx_status kx_batch_get_info(const kx_batch* b, kx_batch_info* out) {
   out->sweep_tiles_per_block = b->tpb;
   out->apply_rounds_per_thread = b->rpt;
   out->sweep_blocks = b->ns;
-  out->apply_blocks = b->na;
+  out->apply_blocks = b->nc;
   out->from_cache = b->from_cache;
   out->tune_ms = b->tune_ms;
   out->batched_launches = b->launches;

@@ -173,6 +173,9 @@ struct SwInst {
   int64_t ld;
   int ldh;
   int a0, na, s0, ns;
+  // the column-march apply launch of steps j >= 1: blocks [c0, c0 + nc),
+  // SW_RED reducers then ncb column blocks on each range of kz planes
+  int c0, nc, ncb, kz;
 };
 
 struct Material {
@@ -315,10 +318,11 @@ kx_status launch_rst_nextvec(kx_ctx* c, cudaStream_t st, int from, int to);
 // `slot`, from its column 0 as set by launch_norm_init (non-augmented)
 kx_status sweep_arnoldi(kx_ctx* c, int slot, int m);
 // the same for every problem of a batch at once (3D FP32, nx % 4 == 0): one
-// launch per Arnoldi phase; tab/aoff/soff device copies of the instance
-// table and of the block offsets (n + 1 entries each), na/ns the launch totals
-kx_status sweep_arnoldi_batch(kx_ctx* c0, cudaStream_t st, const SwInst* tab, const int* aoff, const int* soff, int n,
-                              int na, int ns, int slot, int m, int64_t* launches,
+// launch per Arnoldi phase; tab/aoff/soff/coff device copies of the instance
+// table and of the block offsets of the step-0 apply, sweep and column-march
+// apply launches (n + 1 entries each), na/ns/nc the launch totals
+kx_status sweep_arnoldi_batch(kx_ctx* c0, cudaStream_t st, const SwInst* tab, const int* aoff, const int* soff,
+                              const int* coff, int n, int na, int ns, int nc, int slot, int m, int64_t* launches,
                               std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* sweep_events);
 size_t sweep_smem_bytes();
 const void* sweep_batch_kernel();

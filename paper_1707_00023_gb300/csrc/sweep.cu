@@ -895,6 +895,32 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_sw_pass4s_batch(const SwInst* _
   sw_pass4s_body(I.g, s, I.w[slot], j, I.ld, I.ie, I.sig2, (int)blockIdx.x - I.s0, I.ns);
 }
 
+// Apply pass K_j (j >= 1) of every problem still running, the column march
+// of k_sw_apply_col: the problem's SW_RED reducer blocks, then its column
+// blocks, each over kz planes of NTHREADS quad columns.
+__global__ void __launch_bounds__(NTHREADS, 2) k_sw_apply_col_batch(const SwInst* __restrict__ tab,
+                                                                const int* __restrict__ off, int n, int slot,
+                                                                int j, double btol) {
+  __shared__ SwInst I;
+  const int i = inst_of(off, n, blockIdx.x);
+  load_inst(I, tab, i);
+  pdl_wait();
+  const Slot<float> s = I.s[slot];
+  if (s.st->done || s.st->retired) return;
+  const int bid = (int)blockIdx.x - I.c0;
+  if (bid < SW_RED) {
+    sw_reduce_fin<float>(s, I.w[slot], j, I.ldh, I.ns, btol, bid);
+    return;
+  }
+  const int b = bid - SW_RED;
+  const int zc = b / I.ncb;
+  const int q = (b - zc * I.ncb) * NTHREADS + (int)threadIdx.x;
+  const int k0 = zc * I.kz, k1 = min(I.g.nz, k0 + I.kz);
+  if (q < (I.g.nx >> 2) * I.g.ny && k0 < k1)
+    stencil_column_quad(I.g, s.V + (int64_t)j * I.ld, I.ie, I.sig2, (float*)I.w[slot].t, q, k0, k1);
+  pdl_trigger();
+}
+
 // After the last sweep: one block per problem.
 __global__ void __launch_bounds__(NTHREADS) k_sw_last_batch(const SwInst* __restrict__ tab, int slot, int m,
                                                             double btol) {
@@ -935,8 +961,8 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, size_t smem, cud
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-kx_status sweep_arnoldi_batch(kx_ctx* c0, cudaStream_t st, const SwInst* tab, const int* aoff, const int* soff, int n,
-                              int na, int ns, int slot, int m, int64_t* launches,
+kx_status sweep_arnoldi_batch(kx_ctx* c0, cudaStream_t st, const SwInst* tab, const int* aoff, const int* soff,
+                              const int* coff, int n, int na, int ns, int nc, int slot, int m, int64_t* launches,
                               std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* sweep_events) {
   static SmemOptIn smem{};
   const kx_status so = smem_opt_in(c0, smem, (const void*)k_sw_pass4s_batch, SW_SMEM);
@@ -961,8 +987,10 @@ kx_status sweep_arnoldi_batch(kx_ctx* c0, cudaStream_t st, const SwInst* tab, co
       }
     }
     if (e == cudaSuccess) {
-      e = j == m ? launch_pdl(k_sw_last_batch, n, 0, st, tab, slot, m, bt)
-                 : launch_pdl(k_sw_apply4_batch, na, 0, st, tab, aoff, n, slot, j, bt);
+      // step 0's apply also takes the dots of its finalisation: the quad form
+      e = j == m   ? launch_pdl(k_sw_last_batch, n, 0, st, tab, slot, m, bt)
+          : j == 0 ? launch_pdl(k_sw_apply4_batch, na, 0, st, tab, aoff, n, slot, j, bt)
+                   : launch_pdl(k_sw_apply_col_batch, nc, 0, st, tab, coff, n, slot, j, bt);
       if (e == cudaSuccess) ++*launches;
     }
     if (e != cudaSuccess) {
