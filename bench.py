@@ -446,6 +446,9 @@ def run_uneven(args, w):
                 "e2e": e2e}
         if batch is not None:
             line["autotune"] = tune
+            # batched Arnoldi processes run as replays of their captured graphs
+            # (the event-timed pass above launches directly)
+            line["graph_replays"] = batch.info()["graph_replays"]
         print(json.dumps(line), flush=True)
     if batch is not None:
         batch.close()

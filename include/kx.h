@@ -349,7 +349,11 @@ kx_status response_at_freqs_multi(kx_ctx* const* ctxs, int nctx, const void* con
  * r = 1, 2, 4 (step 0: r quad rounds; later steps: 2 r planes a thread in the
  * column march) -- and keeps the fastest; the choice is cached per size
  * class, the multiset of the problems' grids, for the rest of the process).
- * The timing runs overwrite basis slot 0 of every context.
+ * The timing runs overwrite basis slot 0 of every context.  The batched
+ * Arnoldi process of each basis slot (about 2 m launches) is captured once as a
+ * CUDA graph and replayed at every restart; it is captured again when the
+ * split or krylov_dim changes, and launched directly while per-launch timing
+ * is on (or if a capture fails).
  * Errors: KX_EINVAL (arguments, a context that does not qualify), KX_ENOMEM,
  * KX_ECUDA; text by kx_batch_last_error(NULL). */
 typedef struct kx_batch kx_batch;
@@ -368,6 +372,8 @@ typedef struct {
   double sweep_bytes;           /* their algorithmic bytes: per problem still
                                    running (j+2) n s + 3 ncell s at step j     */
   int64_t sweep_timed_launches;
+  int64_t graph_replays;        /* batched Arnoldi processes launched as one
+                                   replay of their captured CUDA graph         */
 } kx_batch_info;
 kx_status kx_batch_create(kx_ctx* const* ctxs, int nctx, void* cuda_stream, kx_batch** out);
 kx_status kx_batch_destroy(kx_batch* batch);

@@ -60,7 +60,7 @@ class BatchInfo(ctypes.Structure):
                 ("apply_rounds_per_thread", ctypes.c_int), ("sweep_blocks", ctypes.c_int),
                 ("apply_blocks", ctypes.c_int), ("from_cache", ctypes.c_int), ("tune_ms", ctypes.c_double),
                 ("batched_launches", ctypes.c_int64), ("sweep_ms", ctypes.c_double), ("sweep_bytes", ctypes.c_double),
-                ("sweep_timed_launches", ctypes.c_int64)]
+                ("sweep_timed_launches", ctypes.c_int64), ("graph_replays", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):

@@ -47,6 +47,15 @@ struct kx_batch {
   cudaEvent_t ev_arn = nullptr;
   int* h_pin = nullptr;          // pinned host words: per problem MAXF states + a status; one word = 1
   int64_t launches = 0;
+  // the batched Arnoldi process of each basis slot captured once as a CUDA
+  // graph and replayed every restart (re-captured when the launch split or
+  // the Krylov dimension changes; direct launches while tuning or timing)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_m[2] = {0, 0};
+  int64_t graph_count[2] = {0, 0};   // kernel launches one replay holds
+  int64_t graph_replays = 0;
+  bool tuning = false;
+  bool graphs_off = false;           // a capture failed: direct launches from then on
   // per-launch event timing of the batched sweep launches (kx_batch_set_timing)
   int timing = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sweep_events;
@@ -124,12 +133,22 @@ struct StreamSwap {
   }
 };
 
+void drop_graphs(kx_batch* b) {
+  for (int s = 0; s < 2; ++s) {
+    if (b->graph[s]) cudaGraphExecDestroy(b->graph[s]);
+    b->graph[s] = nullptr;
+    b->graph_m[s] = 0;
+    b->graph_count[s] = 0;
+  }
+}
+
 // Launch split for a granularity: problem i gets ns_i = ceil(tiles_i / tpb)
 // sweep blocks, SW_RED + ceil(quads_i / (NTHREADS rpt)) step-0 apply blocks,
 // each capped by its partial-sum stride, and SW_RED + ncb_i ceil(nz_i / kz)
 // column-march apply blocks with kz = 2 rpt planes a block.
 kx_status set_grids(kx_batch* b, int tpb, int rpt) {
   const int n = (int)b->ctx.size();
+  drop_graphs(b);
   b->aoff.assign(n + 1, 0);
   b->soff.assign(n + 1, 0);
   b->coff.assign(n + 1, 0);
@@ -186,8 +205,49 @@ double sweep_bytes_of(const kx_batch* b, int j, const std::vector<char>* active)
   return sum;
 }
 
+// Capture the batched Arnoldi process of a slot (no kernel runs during the
+// capture); false if the capture or its instantiation fails.
+bool capture_process(kx_batch* b, int slot) {
+  const int n = (int)b->ctx.size();
+  const int m = b->ctx[0]->m;
+  if (sweep_batch_prepare(b->ctx[0]) != KX_OK) return false;
+  if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int64_t cnt = 0;
+  const kx_status st = sweep_arnoldi_batch(b->ctx[0], b->stream, b->d_tab, b->d_off, b->d_off + n + 1,
+                                           b->d_off + 2 * (n + 1), n, b->na, b->ns, b->nc, slot, m, &cnt, nullptr);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  bool ok = st == KX_OK && e == cudaSuccess && g != nullptr &&
+            cudaGraphInstantiate(&b->graph[slot], g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();
+    b->graph[slot] = nullptr;
+    return false;
+  }
+  b->graph_m[slot] = m;
+  b->graph_count[slot] = cnt;
+  return true;
+}
+
 kx_status arnoldi_all(kx_batch* b, int slot, const std::vector<char>* active = nullptr) {
   const int n = (int)b->ctx.size();
+  if (!b->timing && !b->tuning && !b->graphs_off) {
+    if (b->graph[slot] && b->graph_m[slot] != b->ctx[0]->m) {
+      cudaGraphExecDestroy(b->graph[slot]);
+      b->graph[slot] = nullptr;
+    }
+    if (!b->graph[slot] && !capture_process(b, slot)) b->graphs_off = true;
+    if (b->graph[slot]) {
+      KB_CUDA(b, cudaGraphLaunch(b->graph[slot], b->stream), "graph launch");
+      b->launches += b->graph_count[slot];
+      b->graph_replays += 1;
+      return KX_OK;
+    }
+  }
   const size_t before = b->sweep_events.size();
   const kx_status st = sweep_arnoldi_batch(b->ctx[0], b->stream, b->d_tab, b->d_off, b->d_off + n + 1,
                                            b->d_off + 2 * (n + 1), n, b->na, b->ns, b->nc, slot, b->ctx[0]->m,
@@ -267,6 +327,12 @@ kx_status autotune(kx_batch* b) {
     }
   }
   StreamSwap swap(b);
+  // the timed candidates launch directly (their Krylov dimension is shortened)
+  struct Tuning {
+    kx_batch* b;
+    ~Tuning() { b->tuning = false; }
+  } tuning{b};
+  b->tuning = true;
   for (kx_ctx* c : b->ctx) {
     k_fill_pattern<<<c->nblk, NTHREADS, 0, b->stream>>>((float*)col_ptr(c, 0, 0), c->n, 0x5bd1e995u);
     KB_CUDA(b, cudaGetLastError(), "start vector");
@@ -403,6 +469,7 @@ kx_status kx_batch_destroy(kx_batch* b) {
   if (!b) return KX_OK;
   if (b->stream) cudaStreamSynchronize(b->stream);
   collect_timing(b);
+  drop_graphs(b);
   if (b->d_tab) cudaFree(b->d_tab);
   if (b->d_off) cudaFree(b->d_off);
   if (b->h_pin) cudaFreeHost(b->h_pin);
@@ -425,6 +492,7 @@ kx_status kx_batch_get_info(const kx_batch* b, kx_batch_info* out) {
   out->sweep_ms = b->sweep_ms;
   out->sweep_bytes = b->sweep_bytes_sum;
   out->sweep_timed_launches = b->sweep_timed;
+  out->graph_replays = b->graph_replays;
   return KX_OK;
 }
 

@@ -321,6 +321,9 @@ kx_status sweep_arnoldi(kx_ctx* c, int slot, int m);
 // launch per Arnoldi phase; tab/aoff/soff/coff device copies of the instance
 // table and of the block offsets of the step-0 apply, sweep and column-march
 // apply launches (n + 1 entries each), na/ns/nc the launch totals
+// the per-device set-up of its launches (dynamic shared memory opt-in), done
+// before a stream capture of them
+kx_status sweep_batch_prepare(kx_ctx* c0);
 kx_status sweep_arnoldi_batch(kx_ctx* c0, cudaStream_t st, const SwInst* tab, const int* aoff, const int* soff,
                               const int* coff, int n, int na, int ns, int nc, int slot, int m, int64_t* launches,
                               std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* sweep_events);

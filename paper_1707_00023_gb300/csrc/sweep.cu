@@ -961,11 +961,15 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, size_t smem, cud
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+kx_status sweep_batch_prepare(kx_ctx* c0) {
+  static SmemOptIn smem{};
+  return smem_opt_in(c0, smem, (const void*)k_sw_pass4s_batch, SW_SMEM);
+}
+
 kx_status sweep_arnoldi_batch(kx_ctx* c0, cudaStream_t st, const SwInst* tab, const int* aoff, const int* soff,
                               const int* coff, int n, int na, int ns, int nc, int slot, int m, int64_t* launches,
                               std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* sweep_events) {
-  static SmemOptIn smem{};
-  const kx_status so = smem_opt_in(c0, smem, (const void*)k_sw_pass4s_batch, SW_SMEM);
+  const kx_status so = sweep_batch_prepare(c0);
   if (so != KX_OK) return so;
   const double bt = sw_btol<float>();
   for (int j = 0; j <= m; ++j) {

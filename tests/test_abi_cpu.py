@@ -67,3 +67,32 @@ def test_create_without_gpu_reports_error():
     # descriptor validation happens before any device call
     d.krylov_dim = 1000
     assert lib.krylov_expm_create(ctypes.byref(d), eps, None, ctypes.byref(h)) == _binding.KX_EINVAL
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding passes by pointer has the size and field
+    offsets the C compiler gives the header's declaration."""
+    import shutil
+    import subprocess
+    from paper_1707_00023_gb300 import _binding as B
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"kx_desc": B.Desc, "kx_stats": B.Stats, "kx_batch_info": B.BatchInfo,
+               "kx_kernel_time": B.KernelTime}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", str(src), "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

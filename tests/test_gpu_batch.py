@@ -42,7 +42,10 @@ def test_batch_matches_single_problems_and_oracle():
     assert info["problems"] == 4 and info["sweep_tiles_per_block"] in (1, 2, 4, 8, 16)
     inten, resid, rst = b.response(gs, oms, T, rtol=1e-7, planes=planes)
     assert np.all(resid <= 1e-7) and np.all(rst >= 1)
-    assert b.info()["batched_launches"] > 0
+    first = b.info()
+    assert first["batched_launches"] > 0
+    # each restart's batched process ran as a replay of its captured graph
+    assert first["graph_replays"] >= int(rst.max())
     for i, sc in enumerate(scs):
         alone = ctxs[i].response_restart_dim(gs[i], sc.omegas, T, rtol=1e-7, plane=sc.plane)
         # the stopping test may fall one restart apart under another reduction order
@@ -53,13 +56,15 @@ def test_batch_matches_single_problems_and_oracle():
             want = yee.intensity(sc.grid, exact.y_plain(A, sc.g, sc.omegas[f], T), sc.plane)
             assert abs(inten[i, f] - want) < 2e-6 * want
     # the same call again gives the same bits (fixed block split and reduction order),
-    # also with the batched sweep launches timed by events
+    # also with the batched sweep launches timed by events (launched directly, not
+    # as graph replays)
     b.set_timing(True)
     again, _, _ = b.response(gs, oms, T, rtol=1e-7, planes=planes)
     b.set_timing(False)
     np.testing.assert_array_equal(again, inten)
     ti = b.info()
     assert ti["sweep_timed_launches"] > 0 and ti["sweep_ms"] > 0.0 and ti["sweep_bytes"] > 0.0
+    assert ti["graph_replays"] == first["graph_replays"]
     b.close()
     # a second batch of the same size class takes the tuned split from the cache
     b2 = Batch(ctxs)
