@@ -241,7 +241,8 @@ __global__ void __launch_bounds__(NTHREADS) k_pass_a(Geo g, SlotSet<T> ss, int j
 // field, 1/eps and basis access is one 16-byte load (helpers in
 // kx_stencil.cuh), and the dots of a chunk of 8 basis columns keep 48 such
 // loads in flight per thread.  The stencil is written out here rather than
-// through stencil_quad: interleaved with the scaling it needs fewer registers.
+// through stencil_quad32: interleaved with the scaling it needs fewer
+// registers.  Its index arithmetic is 32-bit (ncell < 2^31).
 
 // The body of pass A in its quad form; two kernels below instantiate it.
 template <int AUG>
@@ -271,51 +272,54 @@ __device__ __forceinline__ void pass_a4_body(Geo g, SlotSet<float> ss, int j, in
   const int ncol = j + 1;
   const int64_t nc = g.ncell;
   const int64_t nq = nc >> 2;
-  const int64_t nxy = (int64_t)g.nx * g.ny;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nq; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t q4 = base + threadIdx.x;
     const bool act = q4 < nq;
     float4 o[6];
     if (act) {
-      const int64_t c0 = q4 << 2;
-      const int i0 = (int)(c0 % g.nx);
-      const int64_t r = c0 / g.nx;
-      const int jj = (int)(r % g.ny), kk = (int)(r / g.ny);
-      const int jp = (jj + 1 == g.ny) ? 0 : jj + 1, jm = (jj == 0) ? g.ny - 1 : jj - 1;
-      const int kp = (kk + 1 == g.nz) ? 0 : kk + 1, km = (kk == 0) ? g.nz - 1 : kk - 1;
-      const int64_t cjp = c0 + (int64_t)(jp - jj) * g.nx, cjm = c0 + (int64_t)(jm - jj) * g.nx;
-      const int64_t ckp = c0 + (int64_t)(kp - kk) * nxy, ckm = c0 + (int64_t)(km - kk) * nxy;
-      const int ixp = (i0 + 4 == g.nx) ? 0 : i0 + 4;     // first element of the next quad
-      const int ixm = (i0 == 0) ? g.nx - 1 : i0 - 1;     // element before the quad
-      const int64_t cxp = c0 - i0 + ixp, cxm = c0 - i0 + ixm;
-      const float4 Hx = wall4(g, 0, ld4(v + c0), i0, jj, kk);
-      const float4 Hy = wall4(g, 1, ld4(v + nc + c0), i0, jj, kk);
-      const float4 Hz = wall4(g, 2, ld4(v + 2 * nc + c0), i0, jj, kk);
-      const float4 Ex = wall4(g, 3, ld4(v + 3 * nc + c0), i0, jj, kk);
-      const float4 Ey = wall4(g, 4, ld4(v + 4 * nc + c0), i0, jj, kk);
-      const float4 Ez = wall4(g, 5, ld4(v + 5 * nc + c0), i0, jj, kk);
-      const float4 Ez_jp = wall4(g, 5, ld4(v + 5 * nc + cjp), i0, jp, kk);
-      const float4 Ex_jp = wall4(g, 3, ld4(v + 3 * nc + cjp), i0, jp, kk);
-      const float4 Ey_kp = wall4(g, 4, ld4(v + 4 * nc + ckp), i0, jj, kp);
-      const float4 Ex_kp = wall4(g, 3, ld4(v + 3 * nc + ckp), i0, jj, kp);
-      const float4 Hz_jm = wall4(g, 2, ld4(v + 2 * nc + cjm), i0, jm, kk);
-      const float4 Hx_jm = wall4(g, 0, ld4(v + cjm), i0, jm, kk);
-      const float4 Hy_km = wall4(g, 1, ld4(v + nc + ckm), i0, jj, km);
-      const float4 Hx_km = wall4(g, 0, ld4(v + ckm), i0, jj, km);
-      const float Ez_n = wall1(g, 5, v[5 * nc + cxp], ixp, jj, kk);
-      const float Ey_n = wall1(g, 4, v[4 * nc + cxp], ixp, jj, kk);
-      const float Hz_p = wall1(g, 2, v[2 * nc + cxm], ixm, jj, kk);
-      const float Hy_p = wall1(g, 1, v[nc + cxm], ixm, jj, kk);
+      // 32-bit index arithmetic (ncell < 2^31) and the wall tests as
+      // per-component bit masks, as in stencil_quad32
+      const int c0 = (int)(q4 << 2);
+      const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+      const unsigned r = (unsigned)c0 / (unsigned)nx;
+      const int i0 = c0 - (int)r * nx;
+      const unsigned kq = r / (unsigned)ny;
+      const int jj = (int)r - (int)kq * ny, kk = (int)kq;
+      const int jp = (jj + 1 == ny) ? 0 : jj + 1, jm = (jj == 0) ? ny - 1 : jj - 1;
+      const int kp = (kk + 1 == nz) ? 0 : kk + 1, km = (kk == 0) ? nz - 1 : kk - 1;
+      const int cjp = c0 + (jp - jj) * nx, cjm = c0 + (jm - jj) * nx;
+      const int ckp = c0 + (kp - kk) * nxy, ckm = c0 + (km - kk) * nxy;
+      const int ixp = (i0 + 4 == nx) ? 0 : i0 + 4;     // first element of the next quad
+      const int ixm = (i0 == 0) ? nx - 1 : i0 - 1;     // element before the quad
+      const int cxp = c0 - i0 + ixp, cxm = c0 - i0 + ixm;
+      const unsigned xm = wall_bits(g, 0), ym = wall_bits(g, 1), zm = wall_bits(g, 2);
+      const unsigned wx0 = i0 == 0 ? xm : 0u, wy = jj == 0 ? ym : 0u, wz = kk == 0 ? zm : 0u;
+      const unsigned wyp = jp == 0 ? ym : 0u, wym = jm == 0 ? ym : 0u, wzp = kp == 0 ? zm : 0u;
+      const unsigned wzm = km == 0 ? zm : 0u;
+      const unsigned o0 = wx0 | wy | wz, o1 = wy | wz;   // the quad's first cell / the other three
+      const float4 Hx = ldw4(v, c0, o0, o1, 0), Hy = ldw4(v + nc, c0, o0, o1, 1);
+      const float4 Hz = ldw4(v + 2 * nc, c0, o0, o1, 2), Ex = ldw4(v + 3 * nc, c0, o0, o1, 3);
+      const float4 Ey = ldw4(v + 4 * nc, c0, o0, o1, 4), Ez = ldw4(v + 5 * nc, c0, o0, o1, 5);
+      const float4 Ez_jp = ldw4(v + 5 * nc, cjp, wx0 | wyp | wz, wyp | wz, 5);
+      const float4 Ex_jp = ldw4(v + 3 * nc, cjp, wx0 | wyp | wz, wyp | wz, 3);
+      const float4 Ey_kp = ldw4(v + 4 * nc, ckp, wx0 | wy | wzp, wy | wzp, 4);
+      const float4 Ex_kp = ldw4(v + 3 * nc, ckp, wx0 | wy | wzp, wy | wzp, 3);
+      const float4 Hz_jm = ldw4(v + 2 * nc, cjm, wx0 | wym | wz, wym | wz, 2);
+      const float4 Hx_jm = ldw4(v, cjm, wx0 | wym | wz, wym | wz, 0);
+      const float4 Hy_km = ldw4(v + nc, ckm, wx0 | wy | wzm, wy | wzm, 1);
+      const float4 Hx_km = ldw4(v, ckm, wx0 | wy | wzm, wy | wzm, 0);
+      const unsigned wxp = (ixp == 0 ? xm : 0u) | wy | wz, wxm = (ixm == 0 ? xm : 0u) | wy | wz;
+      const float Ez_n = ldw(v + 5 * nc, cxp, wxp, 5), Ey_n = ldw(v + 4 * nc, cxp, wxp, 4);
+      const float Hz_p = ldw(v + 2 * nc, cxm, wxm, 2), Hy_p = ldw(v + nc, cxm, wxm, 1);
       const float4 ie0 = ld4(ie + c0), ie1 = ld4(ie + nc + c0), ie2 = ld4(ie + 2 * nc + c0);
       float4 g4[6];
       if (AUG) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) g4[c] = wall4(g, c, ld4(gsrc + c * nc + c0), i0, jj, kk);
+        for (int c = 0; c < 6; ++c) g4[c] = ldw4(gsrc + c * nc, c0, o0, o1, c);
       }
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const int i = i0 + e;
-        const int li = g.la == 0 ? i : (g.la == 1 ? jj : kk);
+        const int li = g.la == 0 ? i0 + e : (g.la == 1 ? jj : kk);
         float sg[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) sg[c] = sig2[2 * li + g.sighalf[c]];
@@ -335,9 +339,10 @@ __device__ __forceinline__ void pass_a4_body(Geo g, SlotSet<float> ss, int j, in
         out[3] = f4(ie0, e) * (sg[3] * ex - cHx);
         out[4] = f4(ie1, e) * (sg[4] * ey - cHy);
         out[5] = f4(ie2, e) * (sg[5] * ez - cHz);
+        const unsigned me = e == 0 ? o0 : o1;
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-          float x = is_wall(g, c, i, jj, kk) ? 0.f : out[c] * tsj;
+          float x = (me >> c) & 1u ? 0.f : out[c] * tsj;
           if (AUG) x += gco * f4(g4[c], e);
           set4(o[c], e, x);
         }
@@ -351,7 +356,7 @@ __device__ __forceinline__ void pass_a4_body(Geo g, SlotSet<float> ss, int j, in
     float nrm = 0.f;
 #pragma unroll
     for (int c = 0; c < 6; ++c) nrm += dot4(o[c], o[c]);
-    const int64_t c0 = act ? (q4 << 2) : 0;
+    const int64_t cq = act ? (q4 << 2) : 0;
     for (int cb = 0; cb < ncol; cb += 8) {
       float p[8];
 #pragma unroll
@@ -359,7 +364,7 @@ __device__ __forceinline__ void pass_a4_body(Geo g, SlotSet<float> ss, int j, in
         p[t] = 0.f;
         const int col = cb + t;
         if (act && col < ncol) {
-          const float* __restrict__ vc = s.V + (int64_t)col * ld + c0;
+          const float* __restrict__ vc = s.V + (int64_t)col * ld + cq;
 #pragma unroll
           for (int c = 0; c < 6; ++c) p[t] += dot4(ld4(vc + c * nc), o[c]);
         }
@@ -473,7 +478,7 @@ static kx_status pass_a_t(kx_ctx* c, int slot, int ns, int j, const void* gaug) 
   const int ldh = m + 1;
   // the quad kernel needs 16-byte aligned rows of every array it reads
   const bool vec4 = sizeof(T) == 4 && g.dim == 3 && (g.nx % 4) == 0 &&
-                    ((uintptr_t)gaug % 16) == 0;
+                    ((uintptr_t)gaug % 16) == 0 && g.ncell < ((int64_t)1 << 31);
   const int64_t items = vec4 ? g.ncell / 4 : g.ncell;
   const int64_t rounds = (items + NTHREADS - 1) / NTHREADS;
   // the quad kernel in its three-block form when the launch's work (all its
